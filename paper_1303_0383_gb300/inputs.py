@@ -1,0 +1,112 @@
+"""Seeded synthetic inputs for local approximate GP emulation.
+
+This module only draws inputs; it holds none of the method's arithmetic (no
+correlation function, no design criterion, no predictive equation), so both the
+CUDA path and the CPU oracle can take their inputs from it.
+
+The workloads stand in for the paper's own test problems (Sec. 3.4: a 2-d surface
+on a dense 201x201 grid over [-2,2]^2; Sec. 5.2: the 8-d borehole function on an
+LHS), which are not shipped as data.  Shapes follow the five workload
+descriptions below; every draw comes from numpy's PCG64 (``default_rng``) with
+seed 1303038300 + workload number, designs drawn first, then predictive sets,
+then noise.
+
+Arrays are float64, row-major (C order): X is N x p, Z is N, XX is T x p.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 1303038300
+
+
+@dataclasses.dataclass
+class Workload:
+    """One synthetic problem: a design (X, Z), a predictive set XX and the knobs."""
+    name: str
+    X: np.ndarray
+    Z: np.ndarray
+    XX: np.ndarray
+    n0: int
+    n: int
+    ncand: int
+    d: float      # lengthscale theta of exp(-||x-x'||^2 / theta)
+    g: float      # nugget eta
+
+    @property
+    def N(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def p(self) -> int:
+        return int(self.X.shape[1])
+
+    @property
+    def T(self) -> int:
+        return int(self.XX.shape[0])
+
+
+def _surface_2d(X: np.ndarray) -> np.ndarray:
+    # z = x1 * exp(-x1^2 - x2^2): the 2-d response of the tiny and paper-scale workloads
+    return X[:, 0] * np.exp(-X[:, 0] ** 2 - X[:, 1] ** 2)
+
+
+def _surface_8d(X: np.ndarray) -> np.ndarray:
+    # z = sum_j sin(2 pi x_j)/j + x1 x2 x3 + exp(-||x - 0.5||^2)
+    j = np.arange(1, X.shape[1] + 1, dtype=np.float64)
+    s = np.sum(np.sin(2.0 * math.pi * X) / j, axis=1)
+    return s + X[:, 0] * X[:, 1] * X[:, 2] + np.exp(-np.sum((X - 0.5) ** 2, axis=1))
+
+
+def _surface_4d(X: np.ndarray) -> np.ndarray:
+    # z = prod_j sin(3 x_j)
+    return np.prod(np.sin(3.0 * X), axis=1)
+
+
+def _grid(lo: float, hi: float, m: int) -> np.ndarray:
+    g = np.linspace(lo, hi, m)
+    a, b = np.meshgrid(g, g, indexing="ij")
+    return np.ascontiguousarray(np.stack([a.ravel(), b.ravel()], axis=1))
+
+
+def tiny_2d() -> Workload:
+    """N=2000 uniform on [-2,2]^2, 10x10 grid over [-1.9,1.9]^2, d=0.5, g=1e-6, n0=6, n=50, 200 candidates."""
+    rng = np.random.default_rng(SEED_BASE + 1)
+    X = rng.uniform(-2.0, 2.0, size=(2000, 2))
+    XX = _grid(-1.9, 1.9, 10)
+    return Workload("tiny-2d N=2000 T=100 n=50 M=200", X, _surface_2d(X), XX,
+                    n0=6, n=50, ncand=200, d=0.5, g=1e-6)
+
+
+def paper_2d() -> Workload:
+    """N=40000 uniform on [-2,2]^2, 100x100 grid over [-1.97,1.97]^2, d=0.5, g=1e-6, n0=6, n=50, 1000 candidates."""
+    rng = np.random.default_rng(SEED_BASE + 2)
+    X = rng.uniform(-2.0, 2.0, size=(40000, 2))
+    XX = _grid(-1.97, 1.97, 100)
+    return Workload("paper-2d N=40000 T=10000 n=50 M=1000", X, _surface_2d(X), XX,
+                    n0=6, n=50, ncand=1000, d=0.5, g=1e-6)
+
+
+def smooth_8d(T: int = 10000) -> Workload:
+    """N=100000 uniform on [0,1]^8 with N(0, 1e-4) noise, T uniform points, d=1, g=1e-4, n0=8, n=100, 2000 candidates."""
+    rng = np.random.default_rng(SEED_BASE + 3)
+    X = rng.uniform(0.0, 1.0, size=(100000, 8))
+    XX = rng.uniform(0.0, 1.0, size=(10000, 8))[:T]
+    Z = _surface_8d(X) + rng.normal(0.0, math.sqrt(1e-4), size=X.shape[0])
+    return Workload("smooth-8d N=100000 T=%d n=100 M=2000" % T, X, Z, np.ascontiguousarray(XX),
+                    n0=8, n=100, ncand=2000, d=1.0, g=1e-4)
+
+
+def random_case(seed: int, N: int, p: int, T: int, n0: int, n: int, ncand: int,
+                d: float = 0.3, g: float = 1e-6, lo: float = 0.0, hi: float = 1.0) -> Workload:
+    """Small random problem for parity tests: X, XX uniform on [lo,hi]^p, Z a smooth random surface."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(lo, hi, size=(N, p))
+    XX = rng.uniform(lo, hi, size=(T, p))
+    a = rng.normal(size=p)
+    Z = np.sin(X @ a) + 0.5 * np.cos(3.0 * X[:, 0])
+    return Workload("random seed=%d N=%d p=%d T=%d" % (seed, N, p, T), X, Z, XX,
+                    n0=n0, n=n, ncand=ncand, d=d, g=g)
