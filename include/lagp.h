@@ -1,0 +1,151 @@
+/*
+ * lagp.h -- C ABI of liblagp: local approximate Gaussian-process prediction on one GPU.
+ *
+ * Method: R. B. Gramacy and D. W. Apley, "Local Gaussian process approximation for large
+ * computer experiments" (arXiv:1303.0383).  Each predictive location x is an independent
+ * problem (Sec. 4, "Parallelization"):
+ *   (a) the M nearest design points of x form its candidate set, the first n0 of them the
+ *       start design D_{n0} (Sec. 3 intro; Sec. 6 restricts the search to the N' nearest);
+ *   (b) the design grows greedily to n points, each step adding the candidate that
+ *       maximises the ALC reduction in variance (Eq. dxy, Sec. 3.3), minimises the MSPE
+ *       (Eq. mspe, Sec. 3.1), or is simply the next nearest (NN), with the fast
+ *       sequential updates of Sec. 3.2;
+ *   (c) the Student-t predictive equations are evaluated on D_n (Eqs. predgp, preds2).
+ *
+ * Conventions shared by every entry point
+ *   - Arrays are row-major, C order.  X is N x p (float64), Z is N (float64), XX is T x p.
+ *   - Correlation K(a,b) = exp(-||a-b||^2 / theta) for distinct design indices;
+ *     K(a,a) = 1 + g, and K(x,x) = 1 + g for the predictive location (Sec. 2).
+ *   - Squared distances are summed over k = 0..p-1 in that order without fused
+ *     multiply-add, so neighbour sets are reproducible bit for bit; ties in distance go
+ *     to the smaller design index.  Ties in the design criterion go to the nearer
+ *     candidate (smaller neighbour rank).
+ *   - Indices are 0-based int32 design rows; selected indices are in selection order
+ *     (the first n0 are the start design in distance order).
+ *   - Outputs per location: mean = mu_n(x) (Eq. predgp); s2 = psi_n v_n(x) / n, the
+ *     Student-t scale with n degrees of freedom (Eq. preds2); var = s2 n/(n-2), the
+ *     predictive variance.
+ *   - status[t] = 0 on success, or LAGP_ERR_NOT_PD when a chosen point's conditional
+ *     variance is not positive in FP64; that location's outputs are NaN and the rest of
+ *     the batch is unaffected.
+ *
+ * Argument rules (violations return LAGP_ERR_INVALID_ARG before any GPU work):
+ *   N >= 1, p in [1, 8], T >= 0, 1 <= n0 <= n, 3 <= n <= 256, n <= ncand <= min(N, 8192),
+ *   theta > 0, g >= 0, method in lagp_method, precision in lagp_precision,
+ *   MSPE needs n0 >= 3 (its variance uses psi_j/(j-2)).
+ *
+ * Errors: every call returns LAGP_OK (0) or a negative code; nothing is thrown across
+ * the ABI.  lagp_strerror() names a code.  A CUDA failure returns LAGP_ERR_CUDA and
+ * leaves the outputs undefined.
+ *
+ * Threads and streams: calls are thread-safe for distinct output buffers.  The *_dev
+ * entry points enqueue work on the given stream (NULL = legacy default stream) and
+ * return without synchronising; the host entry points synchronise before returning.
+ */
+#ifndef LAGP_H
+#define LAGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LAGP_OK 0
+#define LAGP_ERR_INVALID_ARG (-1)
+#define LAGP_ERR_OOM (-2)
+#define LAGP_ERR_CUDA (-3)
+#define LAGP_ERR_TIMEOUT (-4)
+#define LAGP_ERR_NOT_PD (-5)
+#define LAGP_ERR_NO_DEVICE (-6)
+#define LAGP_ERR_UNSUPPORTED (-7)
+
+typedef enum { LAGP_ALC = 0, LAGP_MSPE = 1, LAGP_NN = 2 } lagp_method;
+
+/* LAGP_FP64: every step in FP64.
+ * LAGP_MIXED: candidate screening in FP32, decisions and all updates in FP64 (the FP64
+ * re-score of the leading candidates decides each greedy step). */
+typedef enum { LAGP_FP64 = 0, LAGP_MIXED = 1 } lagp_precision;
+
+/* Human-readable name of a return code; never NULL, static storage. */
+const char *lagp_strerror(int code);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int lagp_version(void);
+
+/* ------------------------------------------------------------------ host-buffer API */
+
+/* Opaque resident design: the library's device copies of X (N x p) and Z (N).
+ * lagp_design_create copies both from host memory (the caller keeps ownership of its
+ * buffers) onto the current CUDA device; the handle owns the device memory until
+ * lagp_design_destroy.  A design is immutable; concurrent predictions on it are allowed. */
+typedef struct lagp_design lagp_design;
+
+int lagp_design_create(const double *X, const double *Z, int64_t N, int32_t p,
+                       lagp_design **out);
+int lagp_design_destroy(lagp_design *d);
+
+/* Local approximate GP prediction at T host locations XX (T x p) against a resident
+ * design (Secs. 3-4): candidate sets of the ncand nearest, greedy design from n0 to n
+ * by `method`, predictive equations.  Host outputs (caller-owned): mean[T], s2[T];
+ * var[T], idx[T x n] and status[T] may be NULL.  The call copies XX to the device,
+ * runs kernels (a)-(c), copies the results back and synchronises.  Device memory for
+ * inputs, outputs and scratch is allocated and freed inside the call. */
+int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, int32_t n,
+                 int32_t ncand, double theta, double g, int32_t method, int32_t precision,
+                 double *mean, double *s2, double *var, int32_t *idx, int8_t *status);
+
+/* ------------------------------------------------------------------ device-buffer API */
+/* Every pointer below is a device pointer the caller allocated (for example a PyTorch
+ * tensor's storage) and keeps owning.  `workspace` is caller-owned device scratch of at
+ * least the size the matching *_workspace_bytes call returns (contents need not be
+ * initialised; 256-byte alignment required); concurrent calls need distinct workspaces.
+ * `stream` is a cudaStream_t passed as void*. */
+
+/* Scratch bytes lagp_knn_dev needs for T locations against N design points. */
+size_t lagp_knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand);
+
+/* Kernel (a): for each location t, the ncand nearest design points in (d2, index)
+ * order (Sec. 3 intro; Sec. 6, candidate restriction).  X: N x p, XX: T x p;
+ * cand: T x ncand int32 output. */
+int lagp_knn_dev(const double *X, int64_t N, int32_t p, const double *XX, int64_t T,
+                 int32_t ncand, int32_t *cand, void *workspace, size_t workspace_bytes,
+                 void *stream);
+
+/* Scratch bytes lagp_select_dev needs. */
+size_t lagp_select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand,
+                                   int32_t method, int32_t precision);
+
+/* Kernels (b)+(c): greedy local design and predictive equations for T locations whose
+ * candidate lists `cand` (T x ncand, rank order, e.g. from lagp_knn_dev) are given
+ * (Sec. 3.1-3.3 greedy design with the Sec. 3.2 updates; Eqs. predgp, preds2).
+ * Outputs: mean[T], s2[T] required; var[T], idx[T x n], status[T] (int8) may be NULL. */
+int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, const double *XX,
+                    int64_t T, const int32_t *cand, int32_t ncand, int32_t n0, int32_t n,
+                    double theta, double g, int32_t method, int32_t precision, double *mean,
+                    double *s2, double *var, int32_t *idx, int8_t *status, void *workspace,
+                    size_t workspace_bytes, void *stream);
+
+/* Scratch bytes lagp_predict_dev needs (candidate lists plus both kernels' scratch). */
+size_t lagp_predict_workspace_bytes(int64_t N, int64_t T, int32_t p, int32_t n,
+                                    int32_t ncand, int32_t method, int32_t precision);
+
+/* The whole path on device buffers: lagp_knn_dev then lagp_select_dev (the candidate
+ * lists live in the workspace). */
+int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, const double *XX,
+                     int64_t T, int32_t n0, int32_t n, int32_t ncand, double theta, double g,
+                     int32_t method, int32_t precision, double *mean, double *s2, double *var,
+                     int32_t *idx, int8_t *status, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
+/* Number of kernel launches this library has issued in this process (all entry
+ * points, all threads).  Used to report how many of the library's kernels a timed
+ * region launched. */
+int64_t lagp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAGP_H */

@@ -1,0 +1,274 @@
+// api.cu -- the C ABI of liblagp (declared in include/lagp.h): argument checks, the
+// resident design handle, scratch sizing and the host-buffer wrapper around the device
+// path.  All arithmetic of the method runs in the kernels of knn.cu and select.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace lagp {
+
+std::atomic<int64_t> g_launches{0};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LAGP_OK;
+  if (e == cudaErrorMemoryAllocation) return LAGP_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return LAGP_ERR_NO_DEVICE;
+  return LAGP_ERR_CUDA;
+}
+
+int dev_info(DevInfo *out) {
+  static std::mutex mu;
+  static DevInfo cache[64];
+  static bool have[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= 64) return LAGP_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!have[dev]) {
+    DevInfo d;
+    d.device = dev;
+    int v = 0;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    d.num_sms = v;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    d.smem_optin = (size_t)v;
+    cache[dev] = d;
+    have[dev] = true;
+  }
+  *out = cache[dev];
+  return LAGP_OK;
+}
+
+static int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,
+                        double theta, double g, int32_t method, int32_t precision) {
+  if (N < 1 || p < 1 || p > kMaxP || T < 0) return LAGP_ERR_INVALID_ARG;
+  if (N > INT32_MAX || T > INT32_MAX) return LAGP_ERR_INVALID_ARG;
+  if (n0 < 1 || n < n0 || n < 3 || n > kMaxN) return LAGP_ERR_INVALID_ARG;
+  if (ncand < n || (int64_t)ncand > N || ncand > kMaxCand) return LAGP_ERR_INVALID_ARG;
+  if (!(theta > 0.0) || !isfinite(theta) || !(g >= 0.0) || !isfinite(g)) return LAGP_ERR_INVALID_ARG;
+  if (method != LAGP_ALC && method != LAGP_MSPE && method != LAGP_NN) return LAGP_ERR_INVALID_ARG;
+  if (precision != LAGP_FP64 && precision != LAGP_MIXED) return LAGP_ERR_INVALID_ARG;
+  if (method == LAGP_MSPE && n0 < 3) return LAGP_ERR_INVALID_ARG;
+  return LAGP_OK;
+}
+
+static int check_supported(int32_t method, int32_t precision) {
+  if (method == LAGP_MSPE) return LAGP_ERR_UNSUPPORTED;
+  if (precision == LAGP_MIXED && method != LAGP_NN) return LAGP_ERR_UNSUPPORTED;
+  return LAGP_OK;
+}
+
+}  // namespace lagp
+
+using namespace lagp;
+
+struct lagp_design {
+  double *X;
+  double *Z;
+  int64_t N;
+  int32_t p;
+  int device;
+};
+
+extern "C" {
+
+const char *lagp_strerror(int code) {
+  switch (code) {
+    case LAGP_OK: return "ok";
+    case LAGP_ERR_INVALID_ARG: return "invalid argument";
+    case LAGP_ERR_OOM: return "out of device memory";
+    case LAGP_ERR_CUDA: return "CUDA error";
+    case LAGP_ERR_TIMEOUT: return "timed out";
+    case LAGP_ERR_NOT_PD: return "conditional variance not positive (matrix not positive definite in FP64)";
+    case LAGP_ERR_NO_DEVICE: return "no usable CUDA device";
+    case LAGP_ERR_UNSUPPORTED: return "method/precision combination not supported by this build";
+    default: return "unknown error code";
+  }
+}
+
+int lagp_version(void) { return 100; }
+
+int64_t lagp_launch_count(void) { return g_launches.load(); }
+
+int lagp_design_create(const double *X, const double *Z, int64_t N, int32_t p, lagp_design **out) {
+  if (!X || !Z || !out || N < 1 || N > INT32_MAX || p < 1 || p > kMaxP) return LAGP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  lagp_design *d = new (std::nothrow) lagp_design();
+  if (!d) return LAGP_ERR_OOM;
+  d->N = N;
+  d->p = p;
+  d->device = dev;
+  e = cudaMalloc(&d->X, (size_t)N * p * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d->Z, (size_t)N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d->X, X, (size_t)N * p * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d->Z, Z, (size_t)N * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d->X);
+    cudaFree(d->Z);
+    delete d;
+    return cuda_status(e);
+  }
+  *out = d;
+  return LAGP_OK;
+}
+
+int lagp_design_destroy(lagp_design *d) {
+  if (!d) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e1 = cudaFree(d->X);
+  cudaError_t e2 = cudaFree(d->Z);
+  delete d;
+  return cuda_status(e1 != cudaSuccess ? e1 : e2);
+}
+
+size_t lagp_knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand) {
+  DevInfo di;
+  if (dev_info(&di)) return 0;
+  return knn_workspace_bytes(N, T, ncand, di.num_sms);
+}
+
+int lagp_knn_dev(const double *X, int64_t N, int32_t p, const double *XX, int64_t T,
+                 int32_t ncand, int32_t *cand, void *workspace, size_t workspace_bytes,
+                 void *stream) {
+  if (N < 1 || N > INT32_MAX || p < 1 || p > kMaxP || T < 0 || T > INT32_MAX || ncand < 1 ||
+      (int64_t)ncand > N || ncand > kMaxCand)
+    return LAGP_ERR_INVALID_ARG;
+  if (T > 0 && (!X || !XX || !cand || !workspace)) return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  return knn_launch(X, N, p, XX, T, ncand, cand, workspace, workspace_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+size_t lagp_select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
+                                   int32_t precision) {
+  DevInfo di;
+  if (dev_info(&di)) return 0;
+  return select_workspace_bytes(T, p, n, ncand, method, precision, di.num_sms);
+}
+
+int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, const double *XX,
+                    int64_t T, const int32_t *cand, int32_t ncand, int32_t n0, int32_t n,
+                    double theta, double g, int32_t method, int32_t precision, double *mean,
+                    double *s2, double *var, int32_t *idx, int8_t *status, void *workspace,
+                    size_t workspace_bytes, void *stream) {
+  int st = check_common(N, p, T, n0, n, ncand, theta, g, method, precision);
+  if (st) return st;
+  st = check_supported(method, precision);
+  if (st) return st;
+  if (T > 0 && (!X || !Z || !XX || !cand || !mean || !s2 || !workspace)) return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  SelectArgs a;
+  a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
+  a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g;
+  a.method = method; a.precision = precision;
+  a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
+  return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+size_t lagp_predict_workspace_bytes(int64_t N, int64_t T, int32_t p, int32_t n, int32_t ncand,
+                                    int32_t method, int32_t precision) {
+  DevInfo di;
+  if (dev_info(&di)) return 0;
+  size_t cand = align_up((size_t)(T > 0 ? T : 0) * (size_t)ncand * sizeof(int32_t), 256);
+  size_t a = knn_workspace_bytes(N, T, ncand, di.num_sms);
+  size_t b = select_workspace_bytes(T, p, n, ncand, method, precision, di.num_sms);
+  return cand + (a > b ? a : b);
+}
+
+int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, const double *XX,
+                     int64_t T, int32_t n0, int32_t n, int32_t ncand, double theta, double g,
+                     int32_t method, int32_t precision, double *mean, double *s2, double *var,
+                     int32_t *idx, int8_t *status, void *workspace, size_t workspace_bytes,
+                     void *stream) {
+  int st = check_common(N, p, T, n0, n, ncand, theta, g, method, precision);
+  if (st) return st;
+  st = check_supported(method, precision);
+  if (st) return st;
+  if (T == 0) return LAGP_OK;
+  if (!X || !Z || !XX || !mean || !s2 || !workspace) return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  if (workspace_bytes < lagp_predict_workspace_bytes(N, T, p, n, ncand, method, precision))
+    return LAGP_ERR_INVALID_ARG;
+  char *w = static_cast<char *>(workspace);
+  size_t cand_bytes = align_up((size_t)T * (size_t)ncand * sizeof(int32_t), 256);
+  int32_t *cand = reinterpret_cast<int32_t *>(w);
+  void *rest = w + cand_bytes;
+  size_t rest_bytes = workspace_bytes - cand_bytes;
+  st = lagp_knn_dev(X, N, p, XX, T, ncand, cand, rest, rest_bytes, stream);
+  if (st) return st;
+  return lagp_select_dev(X, Z, N, p, XX, T, cand, ncand, n0, n, theta, g, method, precision, mean,
+                         s2, var, idx, status, rest, rest_bytes, stream);
+}
+
+int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, int32_t n,
+                 int32_t ncand, double theta, double g, int32_t method, int32_t precision,
+                 double *mean, double *s2, double *var, int32_t *idx, int8_t *status) {
+  if (!d) return LAGP_ERR_INVALID_ARG;
+  int st = check_common(d->N, d->p, T, n0, n, ncand, theta, g, method, precision);
+  if (st) return st;
+  st = check_supported(method, precision);
+  if (st) return st;
+  if (T == 0) return LAGP_OK;
+  if (!XX || !mean || !s2) return LAGP_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (cur != d->device) {
+    e = cudaSetDevice(d->device);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  cudaStream_t s = cudaStreamPerThread;
+  const size_t nT = (size_t)T, p = (size_t)d->p;
+  const size_t ws_bytes = lagp_predict_workspace_bytes(d->N, T, d->p, n, ncand, method, precision);
+  // One device block: XX | mean | s2 | var | idx | status | workspace
+  size_t off_xx = 0;
+  size_t off_mean = align_up(off_xx + nT * p * sizeof(double), 256);
+  size_t off_s2 = align_up(off_mean + nT * sizeof(double), 256);
+  size_t off_var = align_up(off_s2 + nT * sizeof(double), 256);
+  size_t off_idx = align_up(off_var + nT * sizeof(double), 256);
+  size_t off_st = align_up(off_idx + nT * (size_t)n * sizeof(int32_t), 256);
+  size_t off_ws = align_up(off_st + nT, 256);
+  size_t total = off_ws + ws_bytes;
+  char *buf = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&buf), total, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  double *dXX = reinterpret_cast<double *>(buf + off_xx);
+  double *dmean = reinterpret_cast<double *>(buf + off_mean);
+  double *ds2 = reinterpret_cast<double *>(buf + off_s2);
+  double *dvar = reinterpret_cast<double *>(buf + off_var);
+  int32_t *didx = reinterpret_cast<int32_t *>(buf + off_idx);
+  int8_t *dst = reinterpret_cast<int8_t *>(buf + off_st);
+  e = cudaMemcpyAsync(dXX, XX, nT * p * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = lagp_predict_dev(d->X, d->Z, d->N, d->p, dXX, T, n0, n, ncand, theta, g, method,
+                          precision, dmean, ds2, dvar, didx, dst, buf + off_ws, ws_bytes, s);
+    if (st == LAGP_OK) {
+      e = cudaMemcpyAsync(mean, dmean, nT * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(s2, ds2, nT * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess && var)
+        e = cudaMemcpyAsync(var, dvar, nT * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess && idx)
+        e = cudaMemcpyAsync(idx, didx, nT * (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess && status)
+        e = cudaMemcpyAsync(status, dst, nT, cudaMemcpyDeviceToHost, s);
+    }
+  }
+  cudaError_t ef = cudaFreeAsync(buf, s);
+  cudaError_t es = cudaStreamSynchronize(s);
+  if (cur != d->device) cudaSetDevice(cur);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_status(e);
+  if (ef != cudaSuccess) return cuda_status(ef);
+  return cuda_status(es);
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// internal.h -- declarations shared by the translation units of liblagp (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "lagp.h"
+
+namespace lagp {
+
+// Upper limits checked by the entry points (see the argument rules in lagp.h).
+constexpr int kMaxP = 8;
+constexpr int kMaxN = 256;       // local design size n
+constexpr int kMaxCand = 8192;   // candidate count
+
+extern std::atomic<int64_t> g_launches;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device properties of the current device, cached per device ordinal.
+struct DevInfo {
+  int device;
+  int num_sms;
+  size_t smem_optin;
+};
+int dev_info(DevInfo *out);
+
+// Kernel (a): candidate sets.
+size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms);
+int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
+               int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+// Kernels (b)+(c): greedy design and predictive equations.
+struct SelectArgs {
+  const double *X, *Z;
+  int64_t N;
+  int32_t p;
+  const double *XX;
+  int64_t T;
+  const int32_t *cand;
+  int32_t M, n0, n;
+  double theta, g;
+  int32_t method, precision;
+  double *mean, *s2, *var;
+  int32_t *idx;
+  int8_t *status;
+};
+size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
+                              int32_t precision, int num_sms);
+int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+// Map the last CUDA error to a library code.
+int cuda_status(cudaError_t e);
+
+}  // namespace lagp

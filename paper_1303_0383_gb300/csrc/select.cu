@@ -1,0 +1,263 @@
+// select.cu -- kernels (b)+(c): greedy local design and predictive equations, FP64.
+//
+// Gramacy & Apley, Sec. 3: starting from the n0 nearest neighbours, the local design
+// grows one point at a time; each step adds the candidate c that maximises the ALC
+// reduction in variance at x (Eq. dxy; SM "partial correlations", Eq. dxy2):
+//     score(c) = cov_j(x,c)^2 / v_j(c),
+//     cov_j(a,b) = K(a,b) - k_j(a)^T K_j^{-1} k_j(b),  v_j(c) = cov_j(c,c),
+// or, for NN, simply the next nearest.  Sec. 3.2 requires every step to cost O(j^2)
+// per candidate at most; this kernel costs O(j) per candidate per step by carrying,
+// for every candidate, the row u_c = L_j^{-1} k_j(c) of the bordered Cholesky factor
+// L_j of K_j together with v_j(c) and cov_j(x,c).  Adding point s appends
+//     L_{j+1} = [[L_j, 0], [u_s^T, sqrt(v_j(s))]]
+// (the Cholesky counterpart of the partitioned inverse of SM Sec. 1, with the same
+// Schur-complement scalar v_j(s)), and every candidate updates in O(j):
+//     u_c[j]     = (K(s,c) - u_s . u_c) / sqrt(v_j(s))      (= cov_j(s,c)/sqrt(v_j(s)))
+//     v_{j+1}(c) = v_j(c) - u_c[j]^2                         (Eq. dxy applied at c)
+//     cov_{j+1}(x,c) = cov_j(x,c) - u_x[j] u_c[j].
+// The same recursion gives u_x = L^{-1} k(x) and ytil = L^{-1} Y, hence
+//     psi_{j+1} = psi_j + ytil_j^2   with ytil_j = (y_s - mu_j(s)) / sqrt(v_j(s))
+// (Eq. psiup in the form the SM derives for E{psi_{j+1}}), and at the end
+// mu = u_x . ytil, v_n(x) = K(x,x) - ||u_x||^2, s2 = psi v_n(x)/n, V = psi v_n(x)/(n-2)
+// (Eqs. predgp, preds2).  The start design is built by the same recursion with the
+// pivot forced to ranks 0..n0-1.
+//
+// Layout: one persistent CTA per resident location (a work counter hands out
+// locations).  Per CTA, scratch holds U[j][c] (row j of every candidate, coalesced
+// over c) and the candidates' coordinates Xc[k][c]; v, cov(x,.) and the used flags
+// live in shared memory.
+#include <math.h>
+
+#include "internal.h"
+
+namespace lagp {
+namespace {
+
+constexpr int SB = 256;  // threads per CTA
+
+struct SelParams {
+  const double *X, *Z;
+  int p;
+  const double *XX;
+  int64_t T;
+  const int32_t *cand;
+  int M, Mpad, n0, n, method;
+  double theta_inv, onepg;
+  double *mean, *s2, *var;
+  int32_t *idx;
+  int8_t *status;
+  double *U;      // gridDim.x slots of n x Mpad
+  double *Xc;     // gridDim.x slots of p x Mpad
+  int *queue;
+};
+
+__device__ __forceinline__ bool score_better(double a, int ra, double b, int rb) {
+  return a > b || (a == b && ra < rb);
+}
+
+__global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
+  extern __shared__ __align__(16) double sm[];
+  const int Mpad = P.Mpad, n = P.n, p = P.p, M = P.M;
+  double *v = sm;                       // Mpad
+  double *covx = v + Mpad;              // Mpad
+  double *srow = covx + Mpad;           // n  (u_s, the new row of L)
+  double *ux = srow + n;                // n  (u_x = L^{-1} k(x))
+  double *yt = ux + n;                  // n  (ytil = L^{-1} Y)
+  unsigned char *used = reinterpret_cast<unsigned char *>(yt + n);  // Mpad
+  __shared__ double xs[kMaxP], xl[kMaxP];
+  __shared__ double red_s[SB / 32];
+  __shared__ int red_r[SB / 32];
+  __shared__ int sh_loc, sh_best, sh_fail;
+  __shared__ double sh_inv, sh_uxj, sh_vx, sh_psi;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double *U = P.U + (size_t)blockIdx.x * n * Mpad;
+  double *Xc = P.Xc + (size_t)blockIdx.x * p * Mpad;
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) sh_loc = atomicAdd(P.queue, 1);
+    __syncthreads();
+    const int64_t loc = sh_loc;
+    if (loc >= P.T) break;
+    const int32_t *cnd = P.cand + loc * M;
+    if (tid < p) xl[tid] = P.XX[loc * p + tid];
+    if (tid == 0) { sh_fail = 0; sh_vx = P.onepg; sh_psi = 0.0; }
+    __syncthreads();
+    // Stage candidate coordinates; v = K(c,c) = 1+g, cov_0(x,c) = K(x,c).
+    const int limit = (P.method == LAGP_NN) ? n : M;  // NN never looks past rank n-1
+    for (int c = tid; c < limit; c += SB) {
+      const double *xc = P.X + (int64_t)cnd[c] * p;
+      double acc = 0.0;
+      for (int k = 0; k < p; k++) {
+        double xk = xc[k];
+        Xc[k * Mpad + c] = xk;
+        double t = __dsub_rn(xl[k], xk);
+        acc = __dadd_rn(acc, __dmul_rn(t, t));
+      }
+      v[c] = P.onepg;
+      covx[c] = exp(-acc * P.theta_inv);
+      used[c] = 0;
+    }
+    __syncthreads();
+
+    int s = 0;
+    for (int j = 0; j < n; j++) {
+      if (j >= P.n0 && P.method == LAGP_ALC) s = sh_best;
+      else s = j;
+      if (s < 0) {  // nothing admissible left
+        if (tid == 0) sh_fail = 1;
+        __syncthreads();
+        break;
+      }
+      for (int i = tid; i < j; i += SB) srow[i] = U[(size_t)i * Mpad + s];
+      if (tid < p) xs[tid] = Xc[tid * Mpad + s];
+      __syncthreads();
+      if (tid == 0) {
+        const double vs = v[s];
+        if (!(vs > 0.0)) {
+          sh_fail = 1;
+        } else {
+          const double sq = sqrt(vs);
+          const double uxj = covx[s] / sq;                 // u_x[j]
+          double t = P.Z[cnd[s]];
+          for (int i = 0; i < j; i++) t = fma(-srow[i], yt[i], t);
+          const double ytj = t / sq;                       // ytil[j]
+          ux[j] = uxj;
+          yt[j] = ytj;
+          sh_vx = fma(-uxj, uxj, sh_vx);
+          sh_psi = fma(ytj, ytj, sh_psi);
+          sh_inv = 1.0 / sq;
+          sh_uxj = uxj;
+          used[s] = 1;
+          if (P.idx) P.idx[loc * n + j] = cnd[s];
+        }
+      }
+      __syncthreads();
+      if (sh_fail) break;
+      if (j == n - 1) break;
+      const double inv = sh_inv, uxj = sh_uxj;
+      const bool want_score = (P.method == LAGP_ALC) && (j + 1 >= P.n0);
+      double bs = -INFINITY;
+      int br = 0x7fffffff;
+      for (int c = tid; c < limit; c += SB) {
+        if (used[c]) continue;
+        double acc = 0.0;
+        for (int k = 0; k < p; k++) {
+          double t = __dsub_rn(xs[k], Xc[k * Mpad + c]);
+          acc = __dadd_rn(acc, __dmul_rn(t, t));
+        }
+        double t = exp(-acc * P.theta_inv);                // K(s, c)
+        const double *Uc = U + c;
+        for (int i = 0; i < j; i++) t = fma(-srow[i], Uc[(size_t)i * Mpad], t);
+        const double u = t * inv;                          // u_c[j]
+        U[(size_t)j * Mpad + c] = u;
+        const double vc = fma(-u, u, v[c]);
+        const double cx = fma(-uxj, u, covx[c]);
+        v[c] = vc;
+        covx[c] = cx;
+        if (want_score && vc > 0.0) {
+          const double sc = cx * cx / vc;                  // ALC reduction, Eq. dxy
+          if (score_better(sc, c, bs, br)) { bs = sc; br = c; }
+        }
+      }
+      if (want_score) {
+        for (int o = 16; o > 0; o >>= 1) {
+          double os = __shfl_down_sync(0xffffffffu, bs, o);
+          int orr = __shfl_down_sync(0xffffffffu, br, o);
+          if (score_better(os, orr, bs, br)) { bs = os; br = orr; }
+        }
+        if (lane == 0) { red_s[warp] = bs; red_r[warp] = br; }
+        __syncthreads();
+        if (warp == 0) {
+          bs = (lane < SB / 32) ? red_s[lane] : -INFINITY;
+          br = (lane < SB / 32) ? red_r[lane] : 0x7fffffff;
+          for (int o = 16; o > 0; o >>= 1) {
+            double os = __shfl_down_sync(0xffffffffu, bs, o);
+            int orr = __shfl_down_sync(0xffffffffu, br, o);
+            if (score_better(os, orr, bs, br)) { bs = os; br = orr; }
+          }
+          if (lane == 0) sh_best = (br == 0x7fffffff) ? -1 : br;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (sh_fail) {
+        if (P.status) P.status[loc] = (int8_t)LAGP_ERR_NOT_PD;
+        P.mean[loc] = NAN;
+        P.s2[loc] = NAN;
+        if (P.var) P.var[loc] = NAN;
+      } else {
+        double mu = 0.0;
+        for (int i = 0; i < n; i++) mu = fma(ux[i], yt[i], mu);
+        const double pv = sh_psi * sh_vx;
+        P.mean[loc] = mu;
+        P.s2[loc] = pv / n;
+        if (P.var) P.var[loc] = pv / (n - 2);
+        if (P.status) P.status[loc] = 0;
+      }
+    }
+    if (sh_fail && P.idx) {
+      // A failed location reports no design: every index is -1.
+      for (int i = tid; i < n; i += SB) P.idx[loc * n + i] = -1;
+    }
+  }
+}
+
+int sel_grid(int64_t T, int num_sms) {
+  int64_t g = (int64_t)num_sms * 2;
+  return (int)(T < g ? (T > 0 ? T : 1) : g);
+}
+
+int mpad_of(int M) { return (int)align_up((size_t)M, 32); }
+
+size_t sel_smem_bytes(int Mpad, int n) {
+  return (size_t)(2 * Mpad + 3 * n) * sizeof(double) + align_up((size_t)Mpad, 16);
+}
+
+}  // namespace
+
+size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
+                              int32_t precision, int num_sms) {
+  (void)method;
+  (void)precision;
+  const size_t Mpad = (size_t)mpad_of(ncand);
+  const size_t G = (size_t)sel_grid(T, num_sms);
+  return 256 + align_up(G * (size_t)n * Mpad * sizeof(double), 256) +
+         align_up(G * (size_t)p * Mpad * sizeof(double), 256);
+}
+
+int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (a.T == 0) return LAGP_OK;
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st) return st;
+  if (ws_bytes < select_workspace_bytes(a.T, a.p, a.n, a.M, a.method, a.precision, di.num_sms))
+    return LAGP_ERR_INVALID_ARG;
+  const int Mpad = mpad_of(a.M);
+  const int G = sel_grid(a.T, di.num_sms);
+  char *w = static_cast<char *>(ws);
+  SelParams P;
+  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
+  P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.method = a.method;
+  P.theta_inv = 1.0 / a.theta;
+  P.onepg = 1.0 + a.g;
+  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
+  P.queue = reinterpret_cast<int *>(w);
+  P.U = reinterpret_cast<double *>(w + 256);
+  P.Xc = reinterpret_cast<double *>(w + 256 + align_up((size_t)G * a.n * Mpad * sizeof(double), 256));
+  const size_t smem = sel_smem_bytes(Mpad, a.n);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  select_fp64_kernel<<<G, SB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lagp

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of liblagp (include/lagp.h): the same entry points, argument
+marshalling only.  Every step of the method runs in the library's CUDA kernels; this
+module never computes any of it and has no CPU fallback -- if the library cannot be
+loaded, importing or calling it raises.
+
+Device entry points take torch CUDA tensors (used only as device memory and for
+their stream); host entry points take numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LAGP_OK = 0
+LAGP_ERR_INVALID_ARG = -1
+LAGP_ERR_OOM = -2
+LAGP_ERR_CUDA = -3
+LAGP_ERR_TIMEOUT = -4
+LAGP_ERR_NOT_PD = -5
+LAGP_ERR_NO_DEVICE = -6
+LAGP_ERR_UNSUPPORTED = -7
+
+LAGP_ALC, LAGP_MSPE, LAGP_NN = 0, 1, 2
+LAGP_FP64, LAGP_MIXED = 0, 1
+METHODS = {"alc": LAGP_ALC, "mspe": LAGP_MSPE, "nn": LAGP_NN}
+PRECISIONS = {"fp64": LAGP_FP64, "mixed": LAGP_MIXED}
+
+_lib = None
+
+
+class LagpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s: %s (code %d)" % (what, strerror(code) if _lib else "?", code))
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load liblagp.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise ImportError("liblagp.so not found at %s" % path)
+    L = ctypes.CDLL(path)
+    P, i32, i64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                            ctypes.c_size_t)
+    L.lagp_strerror.argtypes = [ctypes.c_int]
+    L.lagp_strerror.restype = ctypes.c_char_p
+    L.lagp_version.restype = ctypes.c_int
+    L.lagp_launch_count.restype = i64
+    L.lagp_design_create.argtypes = [P, P, i64, i32, ctypes.POINTER(P)]
+    L.lagp_design_destroy.argtypes = [P]
+    L.lagp_predict.argtypes = [P, P, i64, i32, i32, i32, f64, f64, i32, i32, P, P, P, P, P]
+    L.lagp_knn_workspace_bytes.argtypes = [i64, i64, i32]
+    L.lagp_knn_workspace_bytes.restype = sz
+    L.lagp_knn_dev.argtypes = [P, i64, i32, P, i64, i32, P, P, sz, P]
+    L.lagp_select_workspace_bytes.argtypes = [i64, i32, i32, i32, i32, i32]
+    L.lagp_select_workspace_bytes.restype = sz
+    L.lagp_select_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64, i32, i32,
+                                  P, P, P, P, P, P, sz, P]
+    L.lagp_predict_workspace_bytes.argtypes = [i64, i64, i32, i32, i32, i32, i32]
+    L.lagp_predict_workspace_bytes.restype = sz
+    L.lagp_predict_dev.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32, i32,
+                                   P, P, P, P, P, P, sz, P]
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().lagp_strerror(code).decode()
+
+
+def _chk(code: int, what: str) -> None:
+    if code != LAGP_OK:
+        raise LagpError(code, what)
+
+
+def _m(method) -> int:
+    return METHODS[method] if isinstance(method, str) else int(method)
+
+
+def _pr(precision) -> int:
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def lagp_version() -> int:
+    return int(load().lagp_version())
+
+
+def lagp_launch_count() -> int:
+    return int(load().lagp_launch_count())
+
+
+# ----------------------------------------------------------------- device-buffer API
+
+def _dp(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def lagp_knn_workspace_bytes(N: int, T: int, ncand: int) -> int:
+    return int(load().lagp_knn_workspace_bytes(N, T, ncand))
+
+
+def lagp_select_workspace_bytes(T, p, n, ncand, method="alc", precision="fp64") -> int:
+    return int(load().lagp_select_workspace_bytes(T, p, n, ncand, _m(method), _pr(precision)))
+
+
+def lagp_predict_workspace_bytes(N, T, p, n, ncand, method="alc", precision="fp64") -> int:
+    return int(load().lagp_predict_workspace_bytes(N, T, p, n, ncand, _m(method), _pr(precision)))
+
+
+def workspace(nbytes: int, device=None):
+    """A uint8 CUDA tensor usable as library scratch (256-byte aligned by the allocator)."""
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def lagp_knn_dev(X, XX, ncand: int, cand, ws, stream=None) -> None:
+    """Kernel (a) on device tensors: X (N,p) f64, XX (T,p) f64 -> cand (T,ncand) int32."""
+    N, p = X.shape
+    T = XX.shape[0]
+    _chk(load().lagp_knn_dev(_dp(X), N, p, _dp(XX), T, ncand, _dp(cand), _dp(ws), ws.numel(),
+                             _stream(stream)), "lagp_knn_dev")
+
+
+def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2, var=None,
+                    idx=None, status=None, ws=None, stream=None) -> None:
+    """Kernels (b)+(c) on device tensors, candidate lists given."""
+    N, p = X.shape
+    T, M = cand.shape
+    _chk(load().lagp_select_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(cand), M, n0, n, theta, g,
+                                _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
+                                _dp(status), _dp(ws), ws.numel(), _stream(stream)),
+         "lagp_select_dev")
+
+
+def lagp_predict_dev(X, Z, XX, n0, n, ncand, theta, g, method, precision, mean, s2, var=None,
+                     idx=None, status=None, ws=None, stream=None) -> None:
+    """The whole path on device tensors."""
+    N, p = X.shape
+    T = XX.shape[0]
+    _chk(load().lagp_predict_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, n0, n, ncand, theta, g,
+                                 _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
+                                 _dp(status), _dp(ws), ws.numel(), _stream(stream)),
+         "lagp_predict_dev")
+
+
+# ----------------------------------------------------------------- host-buffer API
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Design:
+    """A resident design (lagp_design_create / lagp_design_destroy)."""
+
+    def __init__(self, X, Z):
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.Z = np.ascontiguousarray(Z, dtype=np.float64)
+        self.N, self.p = self.X.shape
+        h = ctypes.c_void_p()
+        _chk(load().lagp_design_create(_hp(self.X), _hp(self.Z), self.N, self.p, ctypes.byref(h)),
+             "lagp_design_create")
+        self._h = h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _chk(load().lagp_design_destroy(self._h), "lagp_design_destroy")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, XX, n0, n, ncand, theta, g, method="alc", precision="fp64", out=None):
+        """lagp_predict on host arrays; returns dict(mean, s2, var, idx, status)."""
+        XX = np.ascontiguousarray(XX, dtype=np.float64)
+        T = XX.shape[0]
+        if out is None:
+            out = dict(mean=np.empty(T), s2=np.empty(T), var=np.empty(T),
+                       idx=np.empty((T, n), np.int32), status=np.empty(T, np.int8))
+        _chk(load().lagp_predict(self._h, _hp(XX), T, n0, n, ncand, theta, g, _m(method),
+                                 _pr(precision), _hp(out["mean"]), _hp(out["s2"]),
+                                 _hp(out.get("var")), _hp(out.get("idx")), _hp(out.get("status"))),
+             "lagp_predict")
+        return out
+
+
+def predict_torch(X, Z, XX, n0, n, ncand, theta, g, method="alc", precision="fp64"):
+    """Convenience: allocate outputs and workspace as torch tensors, run lagp_predict_dev."""
+    import torch
+    dev = X.device
+    T = XX.shape[0]
+    mean = torch.empty(T, dtype=torch.float64, device=dev)
+    s2 = torch.empty_like(mean)
+    var = torch.empty_like(mean)
+    idx = torch.empty((T, n), dtype=torch.int32, device=dev)
+    status = torch.empty(T, dtype=torch.int8, device=dev)
+    ws = workspace(lagp_predict_workspace_bytes(X.shape[0], T, X.shape[1], n, ncand, method,
+                                                precision), dev)
+    lagp_predict_dev(X, Z, XX, n0, n, ncand, theta, g, method, precision, mean, s2, var, idx,
+                     status, ws)
+    return dict(mean=mean, s2=s2, var=var, idx=idx, status=status)

@@ -1,0 +1,56 @@
+"""Parity protocol between the CUDA path and the CPU oracle (test helper).
+
+Selections: the GPU's index sequence is compared with the oracle's step by step.  Where
+they differ, the oracle replays the GPU's choices ("forced path"); at every step where
+the GPU's pick is not the oracle's own best, the oracle's score of the GPU's pick must
+be within SEL_RTOL (relative) of the oracle's best score -- a near-tie that rounding may
+decide either way.  Means and variances are then compared along the same path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+SEL_RTOL = 1e-9      # near-tie margin for selections
+VAL_RTOL = 1e-10     # FP64 form: relative tolerance for mean and s2
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    den = np.maximum(np.abs(b), 1e-300)
+    return np.abs(a - b) / den
+
+
+def check_location(w, t, cand_t, gpu_idx, gpu_mean, gpu_s2, method="alc", val_rtol=VAL_RTOL,
+                   sel_rtol=SEL_RTOL, gpu_var=None):
+    """Check one location; returns a dict with the path used and the errors."""
+    x = w.XX[t]
+    ora = oracle.local_design(w.X, w.Z, x, cand_t, w.n0, w.n, w.d, w.g, method)
+    assert ora["status"] == 0, "oracle failed at location %d" % t
+    # start design is the n0 nearest, in order
+    assert np.array_equal(gpu_idx[: w.n0], cand_t[: w.n0]), "start design differs at %d" % t
+    info = dict(t=t, forced=False, near_ties=0)
+    ref = ora
+    if not np.array_equal(ora["idx"], gpu_idx):
+        f = oracle.local_design(w.X, w.Z, x, cand_t, w.n0, w.n, w.d, w.g, method, forced=gpu_idx)
+        assert f["status"] == 0, "forced replay failed at location %d" % t
+        tr = f["trace"]
+        for k in range(tr.shape[0]):
+            best_rank, best_s, chosen, chosen_s = tr[k, 0], tr[k, 1], tr[k, 2], tr[k, 3]
+            if best_rank != chosen:
+                gap = abs(best_s - chosen_s)
+                assert gap <= sel_rtol * abs(best_s), (
+                    "location %d step %d: GPU chose rank %d (score %.17g), oracle best rank %d "
+                    "(score %.17g), relative gap %.3g > %.1g" %
+                    (t, k + w.n0, chosen, chosen_s, best_rank, best_s, gap / abs(best_s), sel_rtol))
+                info["near_ties"] += 1
+        ref = f
+        info["forced"] = True
+    em = float(rel_err(gpu_mean, ref["mean"]))
+    es = float(rel_err(gpu_s2, ref["s2"]))
+    info.update(err_mean=em, err_s2=es, ref_mean=ref["mean"], ref_s2=ref["s2"])
+    if gpu_var is not None:
+        info["err_var"] = float(rel_err(gpu_var, ref["var"]))
+    info["ok_vals"] = em <= val_rtol and es <= val_rtol and info.get("err_var", 0.0) <= val_rtol
+    return info

@@ -1,0 +1,76 @@
+"""The C ABI library builds (nvcc cross-compiles for sm_103a without a GPU), loads,
+exports every entry point include/lagp.h declares, and rejects bad arguments on the
+host before touching a GPU."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1303_0383_gb300 import lagp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(lagp_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = lagp.load()
+    names = declared_functions()
+    assert len(names) >= 12, names
+    for name in names:
+        assert hasattr(L, name), "missing export %s" % name
+
+
+def test_version_and_error_strings():
+    assert lagp.lagp_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lagp.strerror(code) and lagp.strerror(code) != "unknown error code"
+    assert lagp.strerror(-99) == "unknown error code"
+
+
+def _pred_dev(**kw):
+    a = dict(X=1, Z=1, N=100, p=2, XX=1, T=10, n0=6, n=20, M=50, theta=0.5, g=1e-6, method=0,
+             prec=0, mean=1, s2=1, ws=256, wsb=1 << 20)
+    a.update(kw)
+    P = ctypes.c_void_p
+    return lagp.load().lagp_predict_dev(P(a["X"]), P(a["Z"]), a["N"], a["p"], P(a["XX"]), a["T"],
+                                        a["n0"], a["n"], a["M"], a["theta"], a["g"], a["method"],
+                                        a["prec"], P(a["mean"]), P(a["s2"]), None, None, None,
+                                        P(a["ws"]), a["wsb"], None)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=2), dict(n0=0), dict(n0=21), dict(M=19), dict(M=101), dict(p=0), dict(p=9),
+    dict(theta=0.0), dict(theta=-1.0), dict(theta=float("nan")), dict(g=-1e-9),
+    dict(method=7), dict(prec=5), dict(method=1, n0=2), dict(T=-1), dict(n=300, M=300, N=400),
+    dict(M=9000, N=10000), dict(X=0), dict(ws=0), dict(ws=8),
+])
+def test_invalid_arguments_are_rejected_on_the_host(bad):
+    assert _pred_dev(**bad) == lagp.LAGP_ERR_INVALID_ARG
+
+
+def test_null_design_and_bad_knn_args():
+    L = lagp.load()
+    P = ctypes.c_void_p
+    assert L.lagp_predict(None, None, 1, 6, 20, 50, 0.5, 1e-6, 0, 0, None, None, None, None,
+                          None) == lagp.LAGP_ERR_INVALID_ARG
+    assert L.lagp_design_destroy(None) == lagp.LAGP_ERR_INVALID_ARG
+    out = P()
+    assert L.lagp_design_create(None, None, 10, 2, ctypes.byref(out)) == lagp.LAGP_ERR_INVALID_ARG
+    assert L.lagp_knn_dev(P(1), 10, 2, P(1), 3, 11, P(1), P(256), 1 << 20, None) == \
+        lagp.LAGP_ERR_INVALID_ARG            # ncand > N
+    assert L.lagp_knn_dev(P(1), 10, 2, P(1), 3, 5, P(1), P(8), 1 << 20, None) == \
+        lagp.LAGP_ERR_INVALID_ARG            # misaligned workspace

@@ -1,0 +1,150 @@
+"""CUDA path vs CPU oracle, through the C ABI (needs a GPU)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_0383_gb300 import inputs, lagp
+from tests.parity import check_location, VAL_RTOL
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dev(a, dtype=None):
+    torch = _torch()
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+def gpu_knn(X, XX, M):
+    torch = _torch()
+    Xd, XXd = dev(X, torch.float64), dev(XX, torch.float64)
+    cand = torch.empty((XX.shape[0], M), dtype=torch.int32, device="cuda")
+    ws = lagp.workspace(lagp.lagp_knn_workspace_bytes(X.shape[0], XX.shape[0], M))
+    lagp.lagp_knn_dev(Xd, XXd, M, cand, ws)
+    torch.cuda.synchronize()
+    return cand.cpu().numpy()
+
+
+def gpu_predict(w, method="alc", precision="fp64"):
+    torch = _torch()
+    out = lagp.predict_torch(dev(w.X, torch.float64), dev(w.Z, torch.float64),
+                             dev(w.XX, torch.float64), w.n0, w.n, w.ncand, w.d, w.g, method,
+                             precision)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def run_parity(w, locs=None, method="alc", precision="fp64", val_rtol=VAL_RTOL):
+    g = gpu_predict(w, method, precision)
+    assert (g["status"] == 0).all()
+    locs = range(w.T) if locs is None else locs
+    XXs = w.XX[list(locs)]
+    cand = oracle.knn(w.X, XXs, w.ncand)
+    infos, bad = [], []
+    for k, t in enumerate(locs):
+        info = check_location(w, t, cand[k], g["idx"][t], g["mean"][t], g["s2"][t], method,
+                              val_rtol=val_rtol, gpu_var=g["var"][t])
+        infos.append(info)
+        if not info["ok_vals"]:
+            bad.append(info)
+    return g, infos, bad
+
+
+def test_knn_bit_exact_tiny_2d():
+    w = inputs.tiny_2d()
+    got = gpu_knn(w.X, w.XX, w.ncand)
+    ref = oracle.knn(w.X, w.XX, w.ncand)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("p,N,T,M", [(1, 777, 13, 64), (3, 1234, 37, 97), (8, 3001, 19, 500)])
+def test_knn_bit_exact_random_ragged(p, N, T, M):
+    w = inputs.random_case(11 + p, N, p, T, 3, 10, M)
+    assert np.array_equal(gpu_knn(w.X, w.XX, M), oracle.knn(w.X, w.XX, M))
+
+
+def test_knn_ties_and_boundary_refinement():
+    # many exactly equal distances: duplicated rows force the index tie-break and a
+    # boundary bin larger than shared memory (radix refinement path)
+    rng = np.random.default_rng(5)
+    base = rng.uniform(0, 1, size=(40, 2))
+    X = np.concatenate([np.repeat(base, 250, axis=0), rng.uniform(0, 1, size=(3000, 2))])
+    XX = np.concatenate([base[:5], rng.uniform(0, 1, size=(6, 2))])
+    for M in (100, 1500, 4000):
+        assert np.array_equal(gpu_knn(X, XX, M), oracle.knn(X, XX, M)), M
+
+
+def test_knn_grid_ties():
+    # regular grid design (as in the paper's 201 x 201 illustration): exact ties in d2
+    g = np.linspace(-2, 2, 41)
+    a, b = np.meshgrid(g, g, indexing="ij")
+    X = np.stack([a.ravel(), b.ravel()], 1)
+    XX = np.array([[0.0, 0.0], [0.1, 0.1], [-2.0, 2.0], [0.05, -0.3]])
+    assert np.array_equal(gpu_knn(X, XX, 200), oracle.knn(X, XX, 200))
+
+
+def test_alc_parity_tiny_2d_all_locations():
+    w = inputs.tiny_2d()
+    g, infos, bad = run_parity(w)
+    assert not bad, "value mismatches beyond %.0e: %s" % (VAL_RTOL, bad[:3])
+
+
+def test_nn_parity_tiny_2d():
+    w = inputs.tiny_2d()
+    g, infos, bad = run_parity(w, method="nn")
+    assert not any(i["forced"] for i in infos)
+    assert not bad, bad[:3]
+
+
+@pytest.mark.parametrize("p,seed", [(1, 1), (2, 2), (3, 3), (8, 4)])
+def test_alc_parity_random_small(p, seed):
+    w = inputs.random_case(100 + seed, 300, p, 23, 4, 20, 60, d=0.2 * p, g=1e-6)
+    g, infos, bad = run_parity(w)
+    assert not bad, bad[:3]
+
+
+def test_edge_n0_equals_n_and_m_equals_n():
+    w = inputs.random_case(7, 200, 2, 9, 12, 12, 12)   # no greedy step, M == n
+    g, infos, bad = run_parity(w)
+    assert not bad
+    w = inputs.random_case(8, 200, 2, 9, 3, 12, 12)    # pool exhausted exactly
+    g, infos, bad = run_parity(w)
+    assert not bad
+
+
+def test_single_and_empty_batch():
+    torch = _torch()
+    w = inputs.random_case(9, 300, 2, 1, 4, 15, 40)
+    g, infos, bad = run_parity(w)
+    assert not bad
+    # T = 0 is a no-op that succeeds
+    X = dev(w.X, torch.float64)
+    Z = dev(w.Z, torch.float64)
+    XX = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    lagp.lagp_predict_dev(X, Z, XX, 4, 15, 40, 0.3, 1e-6, "alc", "fp64", e, e, ws=lagp.workspace(256))
+
+
+def test_host_api_matches_device_api():
+    w = inputs.tiny_2d()
+    gd = gpu_predict(w)
+    d = lagp.Design(w.X, w.Z)
+    h = d.predict(w.XX, w.n0, w.n, w.ncand, w.d, w.g)
+    d.close()
+    assert np.array_equal(h["idx"], gd["idx"])
+    assert np.array_equal(h["mean"], gd["mean"]) and np.array_equal(h["s2"], gd["s2"])
+
+
+def test_paper_2d_full_size_sampled():
+    # the full paper-scale workload in the benchmark's launch configuration; the oracle
+    # checks a seeded sample of locations
+    w = inputs.paper_2d()
+    locs = np.random.default_rng(0).choice(w.T, size=40, replace=False)
+    g, infos, bad = run_parity(w, locs=locs)
+    assert not bad, bad[:3]
