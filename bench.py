@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark: local approximate GP predictions per second on one GB300.
+
+Workload (the paper-scale 2-d problem, Sec. 3.4/4.1 scale): design N=40000 uniform on
+[-2,2]^2 with z = x1 exp(-x1^2 - x2^2), 10000 predictive locations on a 100x100 grid
+over [-1.97,1.97]^2, lengthscale d=0.5, nugget g=1e-6, n0=6 -> n=50 by ALC over the
+1000 nearest candidates.  One step = the whole path for all 10000 locations: kernel (a)
+(candidate sets) then kernels (b)+(c) (greedy design + predictive equations).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   # the CPU oracle on host cores (a baseline)
+
+Prints one JSON line.  Under torchrun every rank runs the full workload on its own GPU
+(independent problems, no collective on the data path: weak scaling); `value` is all
+ranks' predictions over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "local-GP predictions/sec (n=50, 1000 cand) FP64 plain vs mixed; serving p99 ms"
+UNIT = "predictions/s"
+FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 flop x max clock
+EXP_FLOPS = 20      # FP64 flops counted per double-precision exp
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources: DRAM counters recorded for another revision are stale."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1303_0383_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(fn.encode())
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def select_flops_per_location(n0, n, M, p, method="alc"):
+    """Algorithmic FP64 flops of the O(j)-per-candidate greedy design for one location:
+    every candidate still in the pool at step j (j = 0..n-2) costs 2j (the Cholesky-row
+    dot) + 3p (squared distance) + 1 + EXP_FLOPS (its correlation to the new point)
+    + 7 (new row entry, v and cov updates, ALC score); plus 3p + 1 + EXP_FLOPS per
+    candidate for K(x, c) at the start."""
+    total = M * (3 * p + 1 + EXP_FLOPS)
+    for j in range(n - 1):
+        pool = M - (j + 1)
+        total += pool * (2 * j + 3 * p + 1 + EXP_FLOPS + 7)
+    return float(total)
+
+
+def paper_form_flops_per_location(n0, n, M):
+    """The paper's O(j^2)-per-candidate form (K_j^{-1} times K(X_j, X_cand) every step)."""
+    return float(sum(2 * j * j * (M - j) for j in range(n0, n)))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], float(parts[3])))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[3] for r in rows)}
+
+
+def cpu_oracle_sample(w, n_loc: int, seed: int = 0):
+    """Times the CPU oracle (as it stands) on a seeded sample of the workload's locations."""
+    import oracle
+    oracle.build()
+    locs = np.sort(np.random.default_rng(seed).choice(w.T, size=n_loc, replace=False))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.predict(w.X, w.Z, w.XX[locs], w.n0, w.n, w.ncand, w.d, w.g, "alc", nthreads=cores)
+    dt = time.perf_counter() - t0
+    assert (r["status"] == 0).all()
+    return n_loc / dt, cores, dt
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_1303_0383_gb300 import inputs
+    w = inputs.paper_2d()
+    sample = args.ref_sample
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, max(8, sample // 8), seed=999)
+    times = []
+    cores = os.cpu_count() or 1
+    for k in range(args.steps):
+        _, cores, dt = cpu_oracle_sample(w, sample, seed=k)
+        times.append(dt)
+    value = sample * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "p": w.p, "T": w.T, "n0": w.n0, "n": w.n,
+                   "ncand": w.ncand, "d": w.d, "g": w.g, "method": "alc",
+                   "step": "oracle on a seeded sample of %d of the %d locations" % (sample, w.T)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d seeded locations per step of the %d" % (sample, w.T)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e_timing(args, w, M, method, prec, flush, idx_dev):
+    """Host entry point lagp_predict with pinned host buffers: the copy of XX in and of
+    every output back are inside each timed call."""
+    import torch
+    from paper_1303_0383_gb300 import lagp
+    T = w.XX.shape[0]
+    design = lagp.Design(w.X, w.Z)
+    XXh = torch.empty((T, w.p), dtype=torch.float64, pin_memory=True).numpy()
+    XXh[:] = w.XX
+    outh = dict(mean=torch.empty(T, dtype=torch.float64, pin_memory=True).numpy(),
+                s2=torch.empty(T, dtype=torch.float64, pin_memory=True).numpy(),
+                var=torch.empty(T, dtype=torch.float64, pin_memory=True).numpy(),
+                idx=torch.empty((T, w.n), dtype=torch.int32, pin_memory=True).numpy(),
+                status=torch.empty(T, dtype=torch.int8, pin_memory=True).numpy())
+    for _ in range(max(1, args.warmup)):
+        design.predict(XXh, w.n0, w.n, M, w.d, w.g, method, prec, out=outh)
+    times = []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        design.predict(XXh, w.n0, w.n, M, w.d, w.g, method, prec, out=outh)
+        times.append(time.perf_counter() - t0)
+    design.close()
+    assert np.array_equal(outh["idx"], idx_dev.cpu().numpy()), "host and device paths disagree"
+    return 1e3 * sum(times) / len(times)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1303_0383_gb300 import inputs, lagp
+    lagp.load()
+    w = inputs.paper_2d()
+    if args.locations:
+        w.XX = np.ascontiguousarray(w.XX[: args.locations])
+        w.name += " (first %d locations)" % args.locations
+    method, prec = "alc", args.precision
+    stream = torch.cuda.current_stream()
+
+    X = torch.as_tensor(w.X).to(dev)
+    Z = torch.as_tensor(w.Z).to(dev)
+    XX = torch.as_tensor(w.XX).to(dev)
+    T, M = w.T, w.ncand
+    cand = torch.empty((T, M), dtype=torch.int32, device=dev)
+    mean = torch.empty(T, dtype=torch.float64, device=dev)
+    s2, var = torch.empty_like(mean), torch.empty_like(mean)
+    idx = torch.empty((T, w.n), dtype=torch.int32, device=dev)
+    status = torch.empty(T, dtype=torch.int8, device=dev)
+    ws_knn = lagp.workspace(lagp.lagp_knn_workspace_bytes(w.N, T, M), dev)
+    ws_sel = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, w.n, M, method, prec), dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        lagp.lagp_knn_dev(X, XX, M, cand, ws_knn, stream)
+        if evs:
+            evs[1].record(stream)
+        lagp.lagp_select_dev(X, Z, XX, cand, w.n0, w.n, w.d, w.g, method, prec, mean, s2, var,
+                             idx, status, ws_sel, stream)
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert int((status != 0).sum()) == 0, "failed locations in warm-up"
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    sampler.start()
+    launches0 = lagp.lagp_launch_count()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.add_(1.0)                 # evict L2 between timed steps (not timed)
+        step(evs[k])
+    barrier()
+    launches = lagp.lagp_launch_count() - launches0
+    knn_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    sel_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [a + b for a, b in zip(knn_ms, sel_ms)]
+    ms_local = sum(step_ms) / len(step_ms)
+
+    # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
+    e2e_ms_local = float("nan")
+    if not args.no_e2e:
+        e2e_ms_local = e2e_timing(args, w, M, method, prec, flush, idx)
+    clocks = sampler.stop()
+
+
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_local, e2e_ms_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(tt[0]), float(tt[1])
+    else:
+        ms, e2e_ms = ms_local, e2e_ms_local
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    value = world * T / (ms / 1e3)
+    sel_avg = sum(sel_ms) / len(sel_ms)
+    flops_loc = select_flops_per_location(w.n0, w.n, M, w.p)
+    achieved = flops_loc * T / (sel_avg / 1e3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "select_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("precision") == prec and tj.get("source_sha256") == kernel_source_hash():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    cpu_val, cores, cpu_dt = (None, None, 0.0) if args.no_cpu else \
+        cpu_oracle_sample(w, min(args.cpu_sample, T))
+    h2d = T * w.p * 8
+    d2h = T * (8 * 3 + 4 * w.n + 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "p": w.p, "T": w.T, "n0": w.n0, "n": w.n,
+                   "ncand": M, "d": w.d, "g": w.g, "method": method, "precision": prec,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas only: each GPU runs the whole workload"},
+        "clocks": clocks,
+        "e2e": {"value": world * T / (e2e_ms / 1e3) if e2e_ms == e2e_ms else None, "unit": UNIT,
+                "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "lagp_predict (host buffers, pinned)"},
+        "gpu_launches": int(launches),
+        "kernels_ms": {"knn": sum(knn_ms) / len(knn_ms), "select": sel_avg},
+        "roofline": {"kernel": "select (kernels b+c)", "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "traffic": traffic,
+                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                     "flops_per_location": flops_loc,
+                     "paper_form_effective_tflops":
+                         paper_form_flops_per_location(w.n0, w.n, M) * T / (sel_avg / 1e3) / 1e12},
+        "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d seeded locations of the %d (%.1f s wall)" %
+                                   (min(args.cpu_sample, T), w.T, cpu_dt)},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-sample", type=int, default=480)
+    ap.add_argument("--ref-sample", type=int, default=160)
+    ap.add_argument("--locations", type=int, default=0,
+                    help="use only the first K locations (small case for profiling)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-API timing")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
