@@ -60,6 +60,7 @@ extern "C" {
 #define LAGP_ERR_NOT_PD (-5)
 #define LAGP_ERR_NO_DEVICE (-6)
 #define LAGP_ERR_UNSUPPORTED (-7)
+#define LAGP_ERR_SCRATCH_LIMIT (-8)
 
 typedef enum { LAGP_ALC = 0, LAGP_MSPE = 1, LAGP_NN = 2 } lagp_method;
 
@@ -138,6 +139,35 @@ int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, con
                      int32_t method, int32_t precision, double *mean, double *s2, double *var,
                      int32_t *idx, int8_t *status, void *workspace, size_t workspace_bytes,
                      void *stream);
+
+/* ------------------------------------------------------------------ no-allocation variant */
+/* Kernels (b)+(c) as lagp_select_dev, for callers that cannot allocate device memory: a
+ * plugin running inside a host application that owns every device allocation and forbids
+ * others once it has started, a real-time loop that cannot afford cudaMalloc's device-wide
+ * synchronisation and unbounded latency, or a process whose allocation budget is spent.
+ * The paper has no counterpart; it is a deployment convenience.
+ *
+ * There is no workspace argument.  The scratch is one static device array of
+ * LAGP_NOALLOC_SCRATCH_BYTES (16 MiB) defined by the library; every device that loads
+ * the library holds it until the process exits.  The call itself allocates nothing (no
+ * cudaMalloc, no cudaFree, no allocating library routine); inputs and outputs are the
+ * caller's device buffers, with the meaning, layout and rules of lagp_select_dev.
+ *   - The first call on a device looks up the array's device address with that device
+ *     current; make that first call before any stream capture.
+ *   - All calls share the array, which keeps the previous call's contents; the call
+ *     clears the part that must start at zero.  Calls whose kernels overlap on the GPU
+ *     (for example on two streams) race on the array: serialise them.
+ *   - The grid is limited to the CTA slots that fit in the array, so a large batch may
+ *     use fewer SMs (and take longer) than lagp_select_dev; results are identical.
+ *   - A problem whose single CTA slot, 256 + (n + p) x ceil32(ncand) x 8 bytes (each
+ *     part rounded up to 256), exceeds the array returns LAGP_ERR_SCRATCH_LIMIT. */
+#define LAGP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t N, int32_t p,
+                            const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                            int32_t n0, int32_t n, double theta, double g, int32_t method,
+                            int32_t precision, double *mean, double *s2, double *var,
+                            int32_t *idx, int8_t *status, void *stream);
 
 /* Number of kernel launches this library has issued in this process (all entry
  * points, all threads).  Used to report how many of the library's kernels a timed

@@ -46,8 +46,8 @@ int dev_info(DevInfo *out) {
   return LAGP_OK;
 }
 
-static int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,
-                        double theta, double g, int32_t method, int32_t precision) {
+int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,
+                 double theta, double g, int32_t method, int32_t precision) {
   if (N < 1 || p < 1 || p > kMaxP || T < 0) return LAGP_ERR_INVALID_ARG;
   if (N > INT32_MAX || T > INT32_MAX) return LAGP_ERR_INVALID_ARG;
   if (n0 < 1 || n < n0 || n < 3 || n > kMaxN) return LAGP_ERR_INVALID_ARG;
@@ -59,7 +59,7 @@ static int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, 
   return LAGP_OK;
 }
 
-static int check_supported(int32_t method, int32_t precision) {
+int check_supported(int32_t method, int32_t precision) {
   if (method == LAGP_MSPE) return LAGP_ERR_UNSUPPORTED;
   if (precision == LAGP_MIXED && method != LAGP_NN) return LAGP_ERR_UNSUPPORTED;
   return LAGP_OK;
@@ -89,6 +89,7 @@ const char *lagp_strerror(int code) {
     case LAGP_ERR_NOT_PD: return "conditional variance not positive (matrix not positive definite in FP64)";
     case LAGP_ERR_NO_DEVICE: return "no usable CUDA device";
     case LAGP_ERR_UNSUPPORTED: return "method/precision combination not supported by this build";
+    case LAGP_ERR_SCRATCH_LIMIT: return "problem too large for the static scratch of the no-allocation entry point";
     default: return "unknown error code";
   }
 }

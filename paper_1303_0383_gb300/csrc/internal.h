@@ -51,6 +51,16 @@ struct SelectArgs {
 size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
                               int32_t precision, int num_sms);
 int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+// The same launch on a caller-chosen grid of G CTAs (G >= 1), and the scratch it needs.
+int select_default_grid(int64_t T, int num_sms);
+size_t select_scratch_bytes_for_grid(int G, int32_t p, int32_t n, int32_t ncand);
+int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
+                          cudaStream_t stream);
+
+// Argument checks shared by the entry points (api.cu).
+int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,
+                 double theta, double g, int32_t method, int32_t precision);
+int check_supported(int32_t method, int32_t precision);
 
 // Map the last CUDA error to a library code.
 int cuda_status(cudaError_t e);

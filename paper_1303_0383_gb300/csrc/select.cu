@@ -260,4 +260,43 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   return cuda_status(cudaGetLastError());
 }
 
+int select_default_grid(int64_t T, int num_sms) { return sel_grid(T, num_sms); }
+
+size_t select_scratch_bytes_for_grid(int G, int32_t p, int32_t n, int32_t ncand) {
+  const size_t Mpad = (size_t)mpad_of(ncand);
+  return 256 + align_up((size_t)G * (size_t)n * Mpad * sizeof(double), 256) +
+         align_up((size_t)G * (size_t)p * Mpad * sizeof(double), 256);
+}
+
+int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
+                          cudaStream_t stream) {
+  if (a.T == 0) return LAGP_OK;
+  if (G < 1) return LAGP_ERR_INVALID_ARG;
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st) return st;
+  if (ws_bytes < select_scratch_bytes_for_grid(G, a.p, a.n, a.M)) return LAGP_ERR_INVALID_ARG;
+  const int Mpad = mpad_of(a.M);
+  char *w = static_cast<char *>(ws);
+  SelParams P;
+  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
+  P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.method = a.method;
+  P.theta_inv = 1.0 / a.theta;
+  P.onepg = 1.0 + a.g;
+  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
+  P.queue = reinterpret_cast<int *>(w);
+  P.U = reinterpret_cast<double *>(w + 256);
+  P.Xc = reinterpret_cast<double *>(w + 256 + align_up((size_t)G * a.n * Mpad * sizeof(double), 256));
+  const size_t smem = sel_smem_bytes(Mpad, a.n);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);   // the work counter starts at zero
+  if (e != cudaSuccess) return cuda_status(e);
+  select_fp64_kernel<<<G, SB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace lagp

@@ -23,6 +23,7 @@ LAGP_ERR_TIMEOUT = -4
 LAGP_ERR_NOT_PD = -5
 LAGP_ERR_NO_DEVICE = -6
 LAGP_ERR_UNSUPPORTED = -7
+LAGP_ERR_SCRATCH_LIMIT = -8
 
 LAGP_ALC, LAGP_MSPE, LAGP_NN = 0, 1, 2
 LAGP_FP64, LAGP_MIXED = 0, 1
@@ -67,6 +68,8 @@ def load(path: str | None = None):
     L.lagp_predict_workspace_bytes.restype = sz
     L.lagp_predict_dev.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32, i32,
                                    P, P, P, P, P, P, sz, P]
+    L.lagp_select_dev_noalloc.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
+                                          i32, i32, P, P, P, P, P, P]
     _lib = L
     return L
 
@@ -148,6 +151,19 @@ def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2
                                 _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
                                 _dp(status), _dp(ws), ws.numel(), _stream(stream)),
          "lagp_select_dev")
+
+
+def lagp_select_dev_noalloc(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2,
+                            var=None, idx=None, status=None, stream=None) -> int:
+    """Kernels (b)+(c) with the library's static scratch (no workspace, no allocation).
+    Returns the library's status code instead of raising, so callers can see
+    LAGP_ERR_SCRATCH_LIMIT."""
+    N, p = X.shape
+    T, M = cand.shape
+    return int(load().lagp_select_dev_noalloc(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(cand), M, n0,
+                                              n, theta, g, _m(method), _pr(precision), _dp(mean),
+                                              _dp(s2), _dp(var), _dp(idx), _dp(status),
+                                              _stream(stream)))
 
 
 def lagp_predict_dev(X, Z, XX, n0, n, ncand, theta, g, method, precision, mean, s2, var=None,

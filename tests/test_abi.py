@@ -36,7 +36,7 @@ def test_library_loads_and_exports_every_declared_symbol():
 
 def test_version_and_error_strings():
     assert lagp.lagp_version() >= 100
-    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert lagp.strerror(code) and lagp.strerror(code) != "unknown error code"
     assert lagp.strerror(-99) == "unknown error code"
 
