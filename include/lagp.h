@@ -169,6 +169,12 @@ int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t N, int32_t
                             int32_t precision, double *mean, double *s2, double *var,
                             int32_t *idx, int8_t *status, void *stream);
 
+/* The library's FP64 exponential (Tang's table-driven method, the one kernels (b)+(c) use
+ * for correlations), evaluated elementwise on device buffers: y[i] = exp(x[i]) for
+ * x[i] in [-707, 0]; arguments below -707 give 0.  For verification against a reference
+ * exponential.  x, y: n doubles (device).  No counterpart in the paper. */
+int lagp_exp_dev(const double *x, double *y, int64_t n, void *stream);
+
 /* Number of kernel launches this library has issued in this process (all entry
  * points, all threads).  Used to report how many of the library's kernels a timed
  * region launched. */

@@ -64,6 +64,7 @@ def _lib(long_double: bool = False):
             L.orc_predict.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32,
                                       P, P, P, P, P, P, i32]
             L.orc_full_gp.argtypes = [P, P, i64, i32, P, f64, f64, P, P]
+            L.orc_design_predict.argtypes = [P, P, i64, i32, P, P, i32, f64, f64, P]
             L.orc_chol.argtypes = [P, i32, P]
             L.orc_inverse.argtypes = [P, i32, P]
             L.orc_pinv_update.argtypes = [P, i32, P, f64, P]
@@ -141,6 +142,17 @@ def predict(X, Z, XX, n0: int, n: int, ncand: int, d: float, g: float, method="a
                                          _p(idx), _p(mean), _p(s2), _p(var), _p(status),
                                          _p(cand), nthreads), "predict")
     return dict(idx=idx, mean=mean, s2=s2, var=var, status=status, cand=cand)
+
+
+def design_predict(X, Z, x, idx, d: float, g: float, long_double: bool = False):
+    """Predictive equations (Eqs. predgp, preds2) at x on the given design indices;
+    returns (mean, s2, var)."""
+    X, Z, x, idx = _f64(X), _f64(Z), _f64(x), _i32(idx)
+    out = np.empty(3)
+    _check(_lib(long_double).orc_design_predict(_p(X), _p(Z), X.shape[0], X.shape[1], _p(x),
+                                                _p(idx), idx.shape[0], d, g, _p(out)),
+           "design_predict")
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def full_gp(X, Z, x, d: float, g: float):

@@ -627,6 +627,45 @@ int orc_predict(const double *X, const double *Z, int64_t N, int32_t p, const do
   return err ? LAGP_ORC_OOM : LAGP_ORC_OK;
 }
 
+/* Predictive equations (Eqs. predgp, preds2) at x on a given design (n design indices):
+ * builds K_n, factors it and returns out = {mean, s2, var}.  Used, in the long-double
+ * build, to adjudicate rounding differences along a fixed design. */
+int orc_design_predict(const double *X, const double *Z, int64_t N, int32_t p, const double *x,
+                       const int32_t *idx, int32_t n, double theta, double g, double *out) {
+  if (n < 3 || N < 1) return LAGP_ORC_INVALID;
+  for (int a = 0; a < n; a++)
+    if (idx[a] < 0 || idx[a] >= N) return LAGP_ORC_INVALID;
+  size_t b = sizeof(real);
+  real *K = malloc(b * n * n), *L = malloc(b * n * n), *kx = malloc(b * n), *y = malloc(b * n);
+  real *ux = malloc(b * n), *yt = malloc(b * n);
+  int st = LAGP_ORC_OOM;
+  if (K && L && kx && y && ux && yt) {
+    for (int a = 0; a < n; a++) {
+      const double *xa = X + (int64_t)idx[a] * p;
+      for (int c = 0; c < n; c++)
+        K[a * n + c] = (a == c) ? 1 + (real)g : corr_r(xa, X + (int64_t)idx[c] * p, p, theta);
+      kx[a] = corr_r(x, xa, p, theta);
+      y[a] = Z[idx[a]];
+    }
+    st = chol_r(K, n, L);
+    if (!st) {
+      fwd_r(L, n, kx, ux);
+      fwd_r(L, n, y, yt);
+      real mu = 0, psi = 0, v = 1 + (real)g;
+      for (int a = 0; a < n; a++) {
+        mu += ux[a] * yt[a];
+        psi += yt[a] * yt[a];
+        v = v - ux[a] * ux[a];
+      }
+      out[0] = (double)mu;
+      out[1] = (double)(psi * v / n);
+      out[2] = (double)(psi * v / (n - 2));
+    }
+  }
+  free(K); free(L); free(kx); free(y); free(ux); free(yt);
+  return st;
+}
+
 /* Full GP at x on the whole design (Eqs. predgp, preds2 with all N points): the
  * special case the local predictor reaches when n = N. */
 int orc_full_gp(const double *X, const double *Z, int64_t N, int32_t p, const double *x,

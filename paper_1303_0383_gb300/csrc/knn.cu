@@ -5,19 +5,24 @@
 // each predictive location x the kernel returns the ncand design indices with the
 // smallest exact FP64 squared distance, ordered by (d2, index).
 //
-// One CTA owns one location at a time (grid-stride over locations):
-//   pass 1  exact d2 for every design point (fixed dimension order, no FMA), written
-//           to the CTA's scratch row, and a 4096-bin histogram of the top 12 bits of
-//           float(d2).  Rounding to float is monotone, so bins order the points
-//           correctly across bins;
-//   select  a block scan of the histogram finds the bin b* holding the ncand-th point;
-//   pass 2  points of bins < b* are certainly selected and go to shared memory; the
-//           points of b* are resolved exactly: copied too when they fit, otherwise by
-//           radix refinement on the 96-bit key (d2 bits, index);
-//   sort    bitonic sort of the shared-memory keys by (d2 bits, index); the first
-//           ncand indices are written out.
-// Non-negative doubles order like their bit patterns, so every exact comparison is an
-// integer comparison of (bits, index) and the result is bit-identical to a full sort.
+// FP64 is 1/58 of FP32 throughput on this GPU, so exact distances are computed only for
+// the few points that can be members.  One CTA owns one location at a time:
+//   prep    (once per call) an FP32 copy of X and B = max |coordinate|;
+//   pass 1  FP32 squared distance d2f of every design point into the CTA's scratch row
+//           and a 4096-bin histogram of the top 12 bits of d2f (non-negative floats order
+//           like their bit patterns);
+//   select  a block scan finds the bin b* holding the ncand-th smallest d2f; tau is the
+//           upper edge of b*;
+//   pass 2  every point with d2f <= tau + 2E survives, where E bounds |d2f - d2| (FP32
+//           rounding of the coordinates, the differences and the fused sum; see
+//           fp32_err_bound) -- all true members survive; survivors get their exact FP64
+//           d2 and go to shared memory;
+//   sort    bitonic sort of the survivors by (d2 bits, index); the first ncand indices
+//           are written out.
+// If the survivors do not fit in shared memory (many points tied at the boundary), the
+// CTA redoes that location exactly in FP64: a 4096-bin histogram of float(d2) over exact
+// d2 in scratch, and radix refinement on the 96-bit key (d2 bits, index) for an
+// oversized boundary bin.  Either way the result is bit-identical to a full sort.
 #include <float.h>
 
 #include "internal.h"
@@ -131,90 +136,175 @@ __device__ void bitonic_sort(uint64_t *key, int32_t *idx, int n2) {
   }
 }
 
+// Bound on |d2f - d2| for a squared distance d2 <= d computed in FP32 from coordinates
+// of magnitude <= B (u = 2^-24): rounding the coordinates and each difference gives
+// |diff_f - diff| <= 2uB + u|diff|, squaring and the p fused additions add (2+p)u d2;
+// summed over k with sum |diff_k| <= sqrt(p d2).  Constants doubled for safety.
+__device__ __forceinline__ double fp32_err_bound(double d, double B, int p) {
+  const double u = 5.9604644775390625e-08;  // 2^-24
+  return 8.0 * u * B * sqrt((double)p * d) + (4.0 + 2.0 * p) * u * d + 16.0 * p * u * u * B * B;
+}
+
+// Exact path for one location (also the fallback): FP64 d2 of every point in scratch D,
+// coarse histogram of float(d2), boundary resolution, keys into skey/sidx; returns count.
+__device__ int knn_exact_location(const double *__restrict__ X, int64_t N, int p, int M,
+                                  const double *xs, double *__restrict__ D, uint64_t *skey,
+                                  int32_t *sidx, uint32_t *hist, int cap, uint32_t *warp_tmp,
+                                  int *sh_bin, uint32_t *sh_below, uint32_t *sh_count,
+                                  uint32_t *pref) {
+  for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
+  if (threadIdx.x == 0) *sh_count = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < N; i += KB) {
+    double d2 = sqdist_exact(xs, X + i * p, p);
+    D[i] = d2;
+    atomicAdd(&hist[coarse_bin(d2)], 1u);
+  }
+  __syncthreads();
+  find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, sh_bin, sh_below);
+  const uint32_t bstar = (uint32_t)*sh_bin;
+  const uint32_t below = *sh_below;
+  const uint32_t nb = hist[bstar];
+  const bool fits = below + nb <= (uint32_t)cap;
+  for (int64_t i = threadIdx.x; i < N; i += KB) {
+    double d2 = D[i];
+    uint32_t b = coarse_bin(d2);
+    if (b < bstar || (fits && b == bstar)) {
+      uint32_t pos = atomicAdd(sh_count, 1u);
+      skey[pos] = (uint64_t)__double_as_longlong(d2);
+      sidx[pos] = (int32_t)i;
+    }
+  }
+  __syncthreads();
+  if (!fits) {
+    uint32_t need = (uint32_t)M - below;
+    uint32_t *h256 = hist;
+    for (int d = 0; d < 12; d++) {
+      for (int b = threadIdx.x; b < 256; b += KB) h256[b] = 0;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < N; i += KB) {
+        double d2 = D[i];
+        if (coarse_bin(d2) != bstar) continue;
+        uint64_t bits = (uint64_t)__double_as_longlong(d2);
+        if (!key_prefix_eq(bits, (uint32_t)i, d, pref)) continue;
+        atomicAdd(&h256[key_digit(bits, (uint32_t)i, d)], 1u);
+      }
+      __syncthreads();
+      const uint32_t cnt0 = *sh_count;  // stable here: no thread appends until after the scan
+      find_rank_bin(h256, 256, need, warp_tmp, sh_bin, sh_below);
+      const uint32_t dd = (uint32_t)*sh_bin, dbelow = *sh_below, deq = h256[dd];
+      const bool last = cnt0 + dbelow + deq <= (uint32_t)cap;
+      for (int64_t i = threadIdx.x; i < N; i += KB) {
+        double d2 = D[i];
+        if (coarse_bin(d2) != bstar) continue;
+        uint64_t bits = (uint64_t)__double_as_longlong(d2);
+        if (!key_prefix_eq(bits, (uint32_t)i, d, pref)) continue;
+        uint32_t dg = key_digit(bits, (uint32_t)i, d);
+        if (dg < dd || (last && dg == dd)) {
+          uint32_t pos = atomicAdd(sh_count, 1u);
+          skey[pos] = bits;
+          sidx[pos] = (int32_t)i;
+        }
+      }
+      __syncthreads();
+      if (last) break;
+      need -= dbelow;
+      if (threadIdx.x == 0) pref[d] = dd;
+      __syncthreads();
+    }
+  }
+  return (int)*sh_count;
+}
+
+__global__ void knn_prep_kernel(const double *__restrict__ X, int64_t n, float *__restrict__ Xf,
+                                unsigned int *__restrict__ bmax) {
+  __shared__ unsigned int wmax[KB / 32];
+  unsigned int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)KB + threadIdx.x; i < n; i += (int64_t)gridDim.x * KB) {
+    const double x = X[i];
+    Xf[i] = __double2float_rn(x);
+    const float a = __double2float_ru(fabs(x));
+    m = max(m, __float_as_uint(a));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < KB / 32; w++) m = max(m, wmax[w]);
+    atomicMax(bmax, m);
+  }
+}
+
 __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, int64_t N, int p,
                                                  const double *__restrict__ XX, int64_t T, int M,
-                                                 int32_t *__restrict__ cand, double *__restrict__ ws,
+                                                 int32_t *__restrict__ cand,
+                                                 const float *__restrict__ Xf,
+                                                 const unsigned int *__restrict__ bmax,
+                                                 float *__restrict__ wsf, double *__restrict__ wsd,
                                                  int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *skey = reinterpret_cast<uint64_t *>(smem);                 // cap
   int32_t *sidx = reinterpret_cast<int32_t *>(skey + cap);             // cap
   uint32_t *hist = reinterpret_cast<uint32_t *>(sidx + cap);           // HBINS
   __shared__ double xs[kMaxP];
+  __shared__ float xf[kMaxP];
   __shared__ uint32_t warp_tmp[32];
   __shared__ int sh_bin;
   __shared__ uint32_t sh_below, sh_count;
   __shared__ uint32_t pref[12];
+  __shared__ float sh_thr;
 
-  double *D = ws + (size_t)blockIdx.x * (size_t)N;
+  float *Df = wsf + (size_t)blockIdx.x * (size_t)N;
+  double *D = wsd + (size_t)blockIdx.x * (size_t)N;
+  const double Bx = (double)__uint_as_float(*bmax);
   for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    if (threadIdx.x < p) xs[threadIdx.x] = XX[t * p + threadIdx.x];
+    if (threadIdx.x < p) {
+      xs[threadIdx.x] = XX[t * p + threadIdx.x];
+      xf[threadIdx.x] = __double2float_rn(xs[threadIdx.x]);
+    }
     for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
     if (threadIdx.x == 0) sh_count = 0;
     __syncthreads();
-    // pass 1: exact distances and coarse histogram
+    // pass 1: FP32 distances and their histogram
     for (int64_t i = threadIdx.x; i < N; i += KB) {
-      double d2 = sqdist_exact(xs, X + i * p, p);
-      D[i] = d2;
-      atomicAdd(&hist[coarse_bin(d2)], 1u);
+      const float *xi = Xf + i * p;
+      float acc = 0.0f;
+      for (int k = 0; k < p; k++) {
+        const float dk = __fsub_rn(xf[k], xi[k]);
+        acc = __fmaf_rn(dk, dk, acc);
+      }
+      Df[i] = acc;
+      atomicAdd(&hist[__float_as_uint(acc) >> (31 - HBITS)], 1u);
     }
     __syncthreads();
     find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, &sh_bin, &sh_below);
-    const uint32_t bstar = (uint32_t)sh_bin;
-    const uint32_t below = sh_below;
-    const uint32_t nb = hist[bstar];
-    const bool fits = below + nb <= (uint32_t)cap;
-    // pass 2: certain members (and the boundary bin when it fits) into shared memory
+    if (threadIdx.x == 0) {
+      double B = Bx;
+      for (int k = 0; k < p; k++) B = fmax(B, fabs(xs[k]));
+      const double tau = (double)__uint_as_float(((uint32_t)sh_bin + 1u) << (31 - HBITS));
+      const double E0 = fp32_err_bound(tau, B, p);
+      const double E = fp32_err_bound(tau + 2.0 * E0, B, p);
+      sh_thr = __double2float_ru(tau + 2.0 * E);
+    }
+    __syncthreads();
+    const float thr = sh_thr;
+    // pass 2: survivors get exact FP64 distances
     for (int64_t i = threadIdx.x; i < N; i += KB) {
-      double d2 = D[i];
-      uint32_t b = coarse_bin(d2);
-      if (b < bstar || (fits && b == bstar)) {
-        uint32_t pos = atomicAdd(&sh_count, 1u);
-        skey[pos] = (uint64_t)__double_as_longlong(d2);
-        sidx[pos] = (int32_t)i;
+      if (Df[i] <= thr) {
+        const double d2 = sqdist_exact(xs, X + i * p, p);
+        const uint32_t pos = atomicAdd(&sh_count, 1u);
+        if (pos < (uint32_t)cap) {
+          skey[pos] = (uint64_t)__double_as_longlong(d2);
+          sidx[pos] = (int32_t)i;
+        }
       }
     }
     __syncthreads();
-    if (!fits) {
-      // Boundary bin too large: radix refinement over its members, 8 bits at a time on
-      // the 96-bit key.  Members below the selected digit are certain; the loop ends
-      // once the remaining tie group fits.  Rare (many equal distances).
-      uint32_t need = (uint32_t)M - below;
-      uint32_t *h256 = hist;  // reuse
-      for (int d = 0; d < 12; d++) {
-        for (int b = threadIdx.x; b < 256; b += KB) h256[b] = 0;
-        __syncthreads();
-        for (int64_t i = threadIdx.x; i < N; i += KB) {
-          double d2 = D[i];
-          if (coarse_bin(d2) != bstar) continue;
-          uint64_t bits = (uint64_t)__double_as_longlong(d2);
-          if (!key_prefix_eq(bits, (uint32_t)i, d, pref)) continue;
-          atomicAdd(&h256[key_digit(bits, (uint32_t)i, d)], 1u);
-        }
-        __syncthreads();
-        const uint32_t cnt0 = sh_count;  // stable here: no thread appends until after the scan
-        find_rank_bin(h256, 256, need, warp_tmp, &sh_bin, &sh_below);
-        const uint32_t dd = (uint32_t)sh_bin, dbelow = sh_below, deq = h256[dd];
-        const bool last = cnt0 + dbelow + deq <= (uint32_t)cap;
-        for (int64_t i = threadIdx.x; i < N; i += KB) {
-          double d2 = D[i];
-          if (coarse_bin(d2) != bstar) continue;
-          uint64_t bits = (uint64_t)__double_as_longlong(d2);
-          if (!key_prefix_eq(bits, (uint32_t)i, d, pref)) continue;
-          uint32_t dg = key_digit(bits, (uint32_t)i, d);
-          if (dg < dd || (last && dg == dd)) {
-            uint32_t pos = atomicAdd(&sh_count, 1u);
-            skey[pos] = bits;
-            sidx[pos] = (int32_t)i;
-          }
-        }
-        __syncthreads();
-        if (last) break;
-        need -= dbelow;
-        if (threadIdx.x == 0) pref[d] = dd;
-        __syncthreads();
-      }
-    }
-    const int cnt = (int)sh_count;
+    int cnt = (int)sh_count;
+    __syncthreads();
+    if (cnt > cap || cnt < M)  // too many ties at the boundary (or, defensively, too few)
+      cnt = knn_exact_location(X, N, p, M, xs, D, skey, sidx, hist, cap, warp_tmp, &sh_bin,
+                               &sh_below, &sh_count, pref);
     int n2 = 1;
     while (n2 < cnt) n2 <<= 1;
     for (int i = cnt + threadIdx.x; i < n2; i += KB) {
@@ -243,9 +333,12 @@ int knn_grid(int64_t T, int num_sms) {
 
 }  // namespace
 
+// Scratch layout: [bmax (256 B)] [Xf: N*p floats] [per CTA: N floats] [per CTA: N doubles]
 size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms) {
   (void)ncand;
-  return align_up((size_t)knn_grid(T, num_sms) * (size_t)N * sizeof(double), 256);
+  const size_t G = (size_t)knn_grid(T, num_sms);
+  return 256 + align_up((size_t)N * kMaxP * sizeof(float), 256) +
+         align_up(G * (size_t)N * sizeof(float), 256) + align_up(G * (size_t)N * sizeof(double), 256);
 }
 
 int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
@@ -262,8 +355,20 @@ int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t 
                                        (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
   const int grid = knn_grid(T, di.num_sms);
-  knn_kernel<<<grid, KB, smem, stream>>>(X, N, p, XX, T, ncand, cand, static_cast<double *>(ws),
-                                         cap);
+  char *w = static_cast<char *>(ws);
+  unsigned int *bmax = reinterpret_cast<unsigned int *>(w);
+  float *Xf = reinterpret_cast<float *>(w + 256);
+  float *wsf = reinterpret_cast<float *>(w + 256 + align_up((size_t)N * kMaxP * sizeof(float), 256));
+  double *wsd = reinterpret_cast<double *>(reinterpret_cast<char *>(wsf) +
+                                           align_up((size_t)grid * N * sizeof(float), 256));
+  e = cudaMemsetAsync(bmax, 0, sizeof(unsigned int), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int64_t n = N * p;
+  int pblocks = (int)((n + KB - 1) / KB);
+  if (pblocks > 4 * di.num_sms) pblocks = 4 * di.num_sms;
+  knn_prep_kernel<<<pblocks, KB, 0, stream>>>(X, n, Xf, bmax);
+  g_launches.fetch_add(1);
+  knn_kernel<<<grid, KB, smem, stream>>>(X, N, p, XX, T, ncand, cand, Xf, bmax, wsf, wsd, cap);
   g_launches.fetch_add(1);
   return cuda_status(cudaGetLastError());
 }

@@ -22,12 +22,16 @@
 // (Eqs. predgp, preds2).  The start design is built by the same recursion with the
 // pivot forced to ranks 0..n0-1.
 //
+// Correlations use the library's table-driven FP64 exponential (fp64_exp.cuh); ALC scores
+// are compared as fractions, without a division per candidate.
+//
 // Layout: one persistent CTA per resident location (a work counter hands out
 // locations).  Per CTA, scratch holds U[j][c] (row j of every candidate, coalesced
 // over c) and the candidates' coordinates Xc[k][c]; v, cov(x,.) and the used flags
 // live in shared memory.
 #include <math.h>
 
+#include "fp64_exp.cuh"
 #include "internal.h"
 
 namespace lagp {
@@ -51,8 +55,12 @@ struct SelParams {
   int *queue;
 };
 
-__device__ __forceinline__ bool score_better(double a, int ra, double b, int rb) {
-  return a > b || (a == b && ra < rb);
+// ALC scores are compared as fractions cov^2 / v without dividing: a/da beats b/db when
+// a*db > b*da (both denominators are positive), ties going to the smaller rank.
+__device__ __forceinline__ bool score_better(double a, double da, int ra, double b, double db,
+                                             int rb) {
+  const double l = a * db, r = b * da;
+  return l > r || (l == r && ra < rb);
 }
 
 __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
@@ -65,8 +73,10 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
   double *yt = ux + n;                  // n  (ytil = L^{-1} Y)
   unsigned char *used = reinterpret_cast<unsigned char *>(yt + n);  // Mpad
   __shared__ double xs[kMaxP], xl[kMaxP];
-  __shared__ double red_s[SB / 32];
+  __shared__ double red_s[SB / 32], red_d[SB / 32];
   __shared__ int red_r[SB / 32];
+  __shared__ double etab[64];
+  if (threadIdx.x < 64) etab[threadIdx.x] = c_exp.tab[threadIdx.x];
   __shared__ int sh_loc, sh_best, sh_fail;
   __shared__ double sh_inv, sh_uxj, sh_vx, sh_psi;
 
@@ -92,11 +102,11 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
       for (int k = 0; k < p; k++) {
         double xk = xc[k];
         Xc[k * Mpad + c] = xk;
-        double t = __dsub_rn(xl[k], xk);
-        acc = __dadd_rn(acc, __dmul_rn(t, t));
+        double t = xl[k] - xk;
+        acc = fma(t, t, acc);
       }
       v[c] = P.onepg;
-      covx[c] = exp(-acc * P.theta_inv);
+      covx[c] = exp_nonpos(-acc * P.theta_inv, etab);
       used[c] = 0;
     }
     __syncthreads();
@@ -138,16 +148,16 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
       if (j == n - 1) break;
       const double inv = sh_inv, uxj = sh_uxj;
       const bool want_score = (P.method == LAGP_ALC) && (j + 1 >= P.n0);
-      double bs = -INFINITY;
+      double bs = -1.0, bd = 1.0;   // best score as a fraction bs/bd (none yet: -1)
       int br = 0x7fffffff;
       for (int c = tid; c < limit; c += SB) {
         if (used[c]) continue;
         double acc = 0.0;
         for (int k = 0; k < p; k++) {
-          double t = __dsub_rn(xs[k], Xc[k * Mpad + c]);
-          acc = __dadd_rn(acc, __dmul_rn(t, t));
+          double t = xs[k] - Xc[k * Mpad + c];
+          acc = fma(t, t, acc);
         }
-        double t = exp(-acc * P.theta_inv);                // K(s, c)
+        double t = exp_nonpos(-acc * P.theta_inv, etab);  // K(s, c)
         const double *Uc = U + c;
         for (int i = 0; i < j; i++) t = fma(-srow[i], Uc[(size_t)i * Mpad], t);
         const double u = t * inv;                          // u_c[j]
@@ -157,25 +167,28 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         v[c] = vc;
         covx[c] = cx;
         if (want_score && vc > 0.0) {
-          const double sc = cx * cx / vc;                  // ALC reduction, Eq. dxy
-          if (score_better(sc, c, bs, br)) { bs = sc; br = c; }
+          const double num = cx * cx;                      // ALC reduction num/vc, Eq. dxy
+          if (score_better(num, vc, c, bs, bd, br)) { bs = num; bd = vc; br = c; }
         }
       }
       if (want_score) {
         for (int o = 16; o > 0; o >>= 1) {
           double os = __shfl_down_sync(0xffffffffu, bs, o);
+          double od = __shfl_down_sync(0xffffffffu, bd, o);
           int orr = __shfl_down_sync(0xffffffffu, br, o);
-          if (score_better(os, orr, bs, br)) { bs = os; br = orr; }
+          if (score_better(os, od, orr, bs, bd, br)) { bs = os; bd = od; br = orr; }
         }
-        if (lane == 0) { red_s[warp] = bs; red_r[warp] = br; }
+        if (lane == 0) { red_s[warp] = bs; red_d[warp] = bd; red_r[warp] = br; }
         __syncthreads();
         if (warp == 0) {
-          bs = (lane < SB / 32) ? red_s[lane] : -INFINITY;
+          bs = (lane < SB / 32) ? red_s[lane] : -1.0;
+          bd = (lane < SB / 32) ? red_d[lane] : 1.0;
           br = (lane < SB / 32) ? red_r[lane] : 0x7fffffff;
           for (int o = 16; o > 0; o >>= 1) {
             double os = __shfl_down_sync(0xffffffffu, bs, o);
+            double od = __shfl_down_sync(0xffffffffu, bd, o);
             int orr = __shfl_down_sync(0xffffffffu, br, o);
-            if (score_better(os, orr, bs, br)) { bs = os; br = orr; }
+            if (score_better(os, od, orr, bs, bd, br)) { bs = os; bd = od; br = orr; }
           }
           if (lane == 0) sh_best = (br == 0x7fffffff) ? -1 : br;
         }
@@ -234,6 +247,8 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   DevInfo di;
   int st = dev_info(&di);
   if (st) return st;
+  st = exp_table_upload();
+  if (st) return st;
   if (ws_bytes < select_workspace_bytes(a.T, a.p, a.n, a.M, a.method, a.precision, di.num_sms))
     return LAGP_ERR_INVALID_ARG;
   const int Mpad = mpad_of(a.M);
@@ -274,6 +289,8 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   if (G < 1) return LAGP_ERR_INVALID_ARG;
   DevInfo di;
   int st = dev_info(&di);
+  if (st) return st;
+  st = exp_table_upload();
   if (st) return st;
   if (ws_bytes < select_scratch_bytes_for_grid(G, a.p, a.n, a.M)) return LAGP_ERR_INVALID_ARG;
   const int Mpad = mpad_of(a.M);

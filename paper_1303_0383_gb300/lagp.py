@@ -68,6 +68,7 @@ def load(path: str | None = None):
     L.lagp_predict_workspace_bytes.restype = sz
     L.lagp_predict_dev.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32, i32,
                                    P, P, P, P, P, P, sz, P]
+    L.lagp_exp_dev.argtypes = [P, P, i64, P]
     L.lagp_select_dev_noalloc.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
                                           i32, i32, P, P, P, P, P, P]
     _lib = L
@@ -151,6 +152,11 @@ def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2
                                 _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
                                 _dp(status), _dp(ws), ws.numel(), _stream(stream)),
          "lagp_select_dev")
+
+
+def lagp_exp_dev(x, y, stream=None) -> None:
+    """The library's FP64 exponential elementwise (device tensors, float64)."""
+    _chk(load().lagp_exp_dev(_dp(x), _dp(y), x.numel(), _stream(stream)), "lagp_exp_dev")
 
 
 def lagp_select_dev_noalloc(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2,

@@ -148,3 +148,28 @@ def test_paper_2d_full_size_sampled():
     locs = np.random.default_rng(0).choice(w.T, size=40, replace=False)
     g, infos, bad = run_parity(w, locs=locs)
     assert not bad, bad[:3]
+
+
+def test_library_exp_against_cuda_and_long_double():
+    """The table-driven FP64 exp used for correlations: within 1 ulp of a long-double
+    reference over the argument range the kernels use, and within 2 ulp of CUDA's exp."""
+    torch = _torch()
+    rng = np.random.default_rng(3)
+    x = np.concatenate([-rng.exponential(1.0, 200000), -rng.uniform(0, 707, 200000),
+                        -np.logspace(-18, 2.8, 20000), [0.0, -0.0, -1e-300, -706.9]])
+    xd = torch.as_tensor(x).cuda()
+    y = torch.empty_like(xd)
+    lagp.lagp_exp_dev(xd, y)
+    ours = y.cpu().numpy()
+    cuda = torch.exp(xd).cpu().numpy()
+    ref = np.exp(x.astype(np.longdouble))
+    ulp = np.spacing(np.abs(ref.astype(np.float64)))
+    err_ref = np.abs(ours.astype(np.longdouble) - ref) / ulp
+    assert float(err_ref.max()) <= 1.0, float(err_ref.max())
+    err_cuda = np.abs(ours - cuda) / ulp
+    assert float(err_cuda.max()) <= 2.0, float(err_cuda.max())
+    assert np.all(lagp_exp_zero_below(x, ours))
+
+
+def lagp_exp_zero_below(x, y):
+    return np.where(x < -707.0, y == 0.0, True)
