@@ -160,7 +160,9 @@ int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, con
  *   - The grid is limited to the CTA slots that fit in the array, so a large batch may
  *     use fewer SMs (and take longer) than lagp_select_dev; results are identical.
  *   - A problem whose single CTA slot, 256 + (n + p) x ceil32(ncand) x 8 bytes (each
- *     part rounded up to 256), exceeds the array returns LAGP_ERR_SCRATCH_LIMIT. */
+ *     part rounded up to 256), exceeds the array returns LAGP_ERR_SCRATCH_LIMIT.
+ *   - Only the FP64 form runs here: precision LAGP_MIXED with ALC returns
+ *     LAGP_ERR_UNSUPPORTED. */
 #define LAGP_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t N, int32_t p,

@@ -24,6 +24,23 @@ void compute_host_consts(ExpConsts *c) {
   c->ln2_64_hi = hi;
   c->ln2_64_lo = (double)(c64 - (long double)hi);
   c->inv_ln2_64 = (double)(64.0L / ln2);
+  for (int j = 0; j < 64; j++) {
+    const long double v = exp2l((long double)j / 64.0L);
+    const float h = (float)v;
+    c->tabf_h[j] = h;
+    c->tabf_l[j] = (float)(v - (long double)h);
+  }
+  float c1 = (float)c64;
+  uint32_t u;
+  memcpy(&u, &c1, sizeof u);
+  u &= ~((1u << 13) - 1);  // 11 significant bits
+  memcpy(&c1, &u, sizeof u);
+  const float c2 = (float)(c64 - (long double)c1);
+  const float c3 = (float)(c64 - (long double)c1 - (long double)c2);
+  c->c1 = c1;
+  c->c2 = c2;
+  c->c3 = c3;
+  c->inv_ln2_64f = (float)(64.0L / ln2);
 }
 
 __global__ void exp_eval_kernel(const double *__restrict__ x, double *__restrict__ y, int64_t n) {

@@ -27,6 +27,10 @@ namespace lagp {
 struct ExpConsts {
   double tab[64];
   double ln2_64_hi, ln2_64_lo, inv_ln2_64;
+  // float-float version: 2^(j/64) = tabf_h + tabf_l; ln2/64 = c1 + c2 + c3 with c1 of 11
+  // significant bits (k * c1 exact for |k| < 2^13).
+  float tabf_h[64], tabf_l[64];
+  float c1, c2, c3, inv_ln2_64f;
 };
 
 // Host: the constants, computed once per process in long double (fp64_exp.cu).

@@ -234,8 +234,8 @@ size_t sel_smem_bytes(int Mpad, int n) {
 
 size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
                               int32_t precision, int num_sms) {
-  (void)method;
-  (void)precision;
+  if (precision == LAGP_MIXED && method == LAGP_ALC)
+    return select_mixed_workspace_bytes(T, p, n, ncand, num_sms);
   const size_t Mpad = (size_t)mpad_of(ncand);
   const size_t G = (size_t)sel_grid(T, num_sms);
   return 256 + align_up(G * (size_t)n * Mpad * sizeof(double), 256) +
@@ -244,6 +244,8 @@ size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, in
 
 int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
   if (a.T == 0) return LAGP_OK;
+  if (a.precision == LAGP_MIXED && a.method == LAGP_ALC)
+    return select_mixed_launch(a, ws, ws_bytes, stream);
   DevInfo di;
   int st = dev_info(&di);
   if (st) return st;

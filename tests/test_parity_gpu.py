@@ -173,3 +173,38 @@ def test_library_exp_against_cuda_and_long_double():
 
 def lagp_exp_zero_below(x, y):
     return np.where(x < -707.0, y == 0.0, True)
+
+
+# ----------------------------------------------------------------- mixed precision
+
+def test_mixed_parity_tiny_2d_all_locations():
+    w = inputs.tiny_2d()
+    g, infos, bad = run_parity(w, precision="mixed")
+    assert not bad, bad[:3]
+
+
+@pytest.mark.parametrize("p,seed", [(1, 1), (2, 2), (3, 3), (8, 4)])
+def test_mixed_parity_random_small(p, seed):
+    w = inputs.random_case(100 + seed, 300, p, 23, 4, 20, 60, d=0.2 * p, g=1e-6)
+    g, infos, bad = run_parity(w, precision="mixed")
+    assert not bad, bad[:3]
+
+
+def test_mixed_edge_cases():
+    for w in (inputs.random_case(7, 200, 2, 9, 12, 12, 12), inputs.random_case(8, 200, 2, 9, 3, 12, 12),
+              inputs.random_case(9, 300, 2, 1, 4, 15, 40)):
+        g, infos, bad = run_parity(w, precision="mixed")
+        assert not bad, bad[:3]
+
+
+def test_mixed_paper_2d_full_size_sampled_and_agrees_with_fp64():
+    w = inputs.paper_2d()
+    locs = np.random.default_rng(1).choice(w.T, size=40, replace=False)
+    g, infos, bad = run_parity(w, locs=locs, precision="mixed")
+    assert not bad, bad[:3]
+    f = gpu_predict(w, precision="fp64")
+    same = (f["idx"] == g["idx"]).all(axis=1)
+    # designs differ only where some step was a near-tie within FP64 rounding
+    assert same.mean() >= 0.999, same.mean()
+    rel = np.abs(f["s2"][same] - g["s2"][same]) / f["s2"][same]
+    assert rel.max() <= 1e-9, rel.max()
