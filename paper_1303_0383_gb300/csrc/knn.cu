@@ -265,16 +265,19 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
     if (threadIdx.x == 0) sh_count = 0;
     __syncthreads();
-    // pass 1: FP32 distances and their histogram
-    for (int64_t i = threadIdx.x; i < N; i += KB) {
-      const float *xi = Xf + i * p;
-      float acc = 0.0f;
-      for (int k = 0; k < p; k++) {
-        const float dk = __fsub_rn(xf[k], xi[k]);
-        acc = __fmaf_rn(dk, dk, acc);
+    // pass 1: FP32 distances and their histogram (32-bit indices: N < 2^31)
+    const int Ni = (int)N;
+    {
+      const float *xi = Xf + threadIdx.x * p;
+      for (int i = threadIdx.x; i < Ni; i += KB, xi += KB * p) {
+        float acc = 0.0f;
+        for (int k = 0; k < p; k++) {
+          const float dk = __fsub_rn(xf[k], xi[k]);
+          acc = __fmaf_rn(dk, dk, acc);
+        }
+        Df[i] = acc;
+        atomicAdd(&hist[__float_as_uint(acc) >> (31 - HBITS)], 1u);
       }
-      Df[i] = acc;
-      atomicAdd(&hist[__float_as_uint(acc) >> (31 - HBITS)], 1u);
     }
     __syncthreads();
     find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, &sh_bin, &sh_below);
@@ -289,9 +292,9 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     __syncthreads();
     const float thr = sh_thr;
     // pass 2: survivors get exact FP64 distances
-    for (int64_t i = threadIdx.x; i < N; i += KB) {
+    for (int i = threadIdx.x; i < Ni; i += KB) {
       if (Df[i] <= thr) {
-        const double d2 = sqdist_exact(xs, X + i * p, p);
+        const double d2 = sqdist_exact(xs, X + (size_t)i * p, p);
         const uint32_t pos = atomicAdd(&sh_count, 1u);
         if (pos < (uint32_t)cap) {
           skey[pos] = (uint64_t)__double_as_longlong(d2);

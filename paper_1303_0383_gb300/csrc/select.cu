@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         }
         double t = exp_nonpos(-acc * P.theta_inv, etab);  // K(s, c)
         const double *Uc = U + c;
-        for (int i = 0; i < j; i++) t = fma(-srow[i], Uc[(size_t)i * Mpad], t);
+        for (int i = 0; i < j; i++, Uc += Mpad) t = fma(-srow[i], *Uc, t);
         const double u = t * inv;                          // u_c[j]
         U[(size_t)j * Mpad + c] = u;
         const double vc = fma(-u, u, v[c]);

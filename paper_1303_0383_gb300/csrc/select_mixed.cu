@@ -15,6 +15,10 @@
 // Otherwise the screen's best is taken.  DELTA = 1e-5 is about five times the largest
 // screen-vs-FP64 score discrepancy measured by emulation (2e-6 of the best score).
 //
+// Each thread screens a pair of candidates with packed FP32 instructions (ff2.cuh), and a
+// step needs one block barrier: every thread merges the per-warp best/second-best results
+// and derives the step's pivot scalars itself.
+//
 // After the last step the predictive equations (Eqs. predgp, preds2) are evaluated in
 // FP64 on the final design: K_n augmented with the columns k(x) and Y is factored by a
 // right-looking Cholesky, which performs for every entry the same subtractions in the
@@ -23,6 +27,7 @@
 #include <math.h>
 
 #include "ff.cuh"
+#include "ff2.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -39,48 +44,51 @@ struct MixParams {
   const double *XX;
   int64_t T;
   const int32_t *cand;
-  int M, Mpad, n0, n;
+  int M, Mpad, Qpad, n0, n;
   double theta, theta_inv, g, onepg;
   double *mean, *s2, *var;
   int32_t *idx;
   int8_t *status;
-  ff *U;         // slots of n x Mpad
-  ff *Xr;        // slots of p x Mpad: candidate coordinates minus x
+  float4 *U;     // slots of n x Qpad candidate pairs: row j of every candidate's factor row
+  float4 *Xr;    // slots of p x Qpad pairs: candidate coordinates minus x
   double *A;     // slots of n x (n + 2): FP64 factorisation
   int *queue;
   int *rescores; // count of FP64 re-score passes (diagnostics)
 };
 
-// exp(a) for a <= 0 in float-float (Tang's table-driven method with N = 64, see
+// exp(a) for a <= 0 on a pair, in float-float (Tang's table-driven method with N = 64, see
 // fp64_exp.cuh): a = k ln2/64 + r, exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 with
 // the first two terms in float-float and the rest in FP32 (they are below 3e-8).
-__device__ __forceinline__ ff exp_ff(ff a, const float *tabh, const float *tabl) {
-  if (a.h < -87.0f) return ff{0.0f, 0.0f};
-  const float magic = 12582912.0f;  // 1.5 * 2^23
-  const float t = __fmaf_rn(a.h, c_exp.inv_ln2_64f, magic);
-  const float kf = __fsub_rn(t, magic);
-  const int k = __float_as_int(t) - 0x4B400000;
-  const float r1 = __fmaf_rn(-kf, c_exp.c1, a.h);  // exact
-  const float p2h = __fmul_rn(kf, c_exp.c2);
-  const float p2l = __fmaf_rn(kf, c_exp.c2, -p2h);
-  const ff s = two_sum(r1, -p2h);
-  const float rl = __fadd_rn(__fsub_rn(__fsub_rn(s.l, p2l), __fmul_rn(kf, c_exp.c3)), a.l);
-  const ff r = fast_two_sum(s.h, rl);
-  const float sqh = __fmul_rn(r.h, r.h);
-  const float sql = __fmaf_rn(2.0f * r.h, r.l, __fmaf_rn(r.h, r.h, -sqh));
-  const float P = __fmul_rn(__fmul_rn(r.h, sqh),
-                            __fmaf_rn(r.h, __fmaf_rn(r.h, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f));
-  const ff e = two_sum(r.h, 0.5f * sqh);
-  const ff E = fast_two_sum(e.h, __fadd_rn(__fadd_rn(e.l, r.l), __fmaf_rn(0.5f, sql, P)));
-  const int j = k & 63;
-  const float Th = tabh[j], Tl = tabl[j];
-  const float ph = __fmul_rn(Th, E.h);
-  const float pl = __fmaf_rn(Th, E.h, -ph);
-  const ff s2 = two_sum(Th, ph);
-  const float low = __fadd_rn(__fadd_rn(s2.l, pl), __fmaf_rn(Th, E.l, __fmaf_rn(Tl, E.h, Tl)));
-  const ff res = fast_two_sum(s2.h, low);
-  const float sc = __int_as_float(((k >> 6) + 127) << 23);
-  return ff{__fmul_rn(res.h, sc), __fmul_rn(res.l, sc)};
+// Arguments below -87 give 0.
+__device__ __forceinline__ ff2 exp_ff2(ff2 a, const float *tabh, const float *tabl) {
+  const float2 ah = make_float2(fmaxf(a.h.x, -87.0f), fmaxf(a.h.y, -87.0f));
+  const float2 magic = f2s(12582912.0f);  // 1.5 * 2^23
+  const float2 t = fma2(ah, f2s(c_exp.inv_ln2_64f), magic);
+  const float2 kf = sub2(t, magic);
+  const int kx = __float_as_int(t.x) - 0x4B400000, ky = __float_as_int(t.y) - 0x4B400000;
+  const float2 r1 = fma2(neg2(kf), f2s(c_exp.c1), ah);  // exact
+  const float2 p2h = mul2(kf, f2s(c_exp.c2));
+  const float2 p2l = fma2(kf, f2s(c_exp.c2), neg2(p2h));
+  const ff2 s = two_sum2(r1, neg2(p2h));
+  const float2 rl = add2(sub2(sub2(s.l, p2l), mul2(kf, f2s(c_exp.c3))), a.l);
+  const ff2 r = fast_two_sum2(s.h, rl);
+  const float2 sqh = mul2(r.h, r.h);
+  const float2 sql = fma2(add2(r.h, r.h), r.l, fma2(r.h, r.h, neg2(sqh)));
+  const float2 P = mul2(mul2(r.h, sqh),
+                        fma2(r.h, fma2(r.h, f2s(1.0f / 120.0f), f2s(1.0f / 24.0f)), f2s(1.0f / 6.0f)));
+  const ff2 e = two_sum2(r.h, mul2(f2s(0.5f), sqh));
+  const ff2 E = fast_two_sum2(e.h, add2(add2(e.l, r.l), fma2(f2s(0.5f), sql, P)));
+  const float2 Th = f2(tabh[kx & 63], tabh[ky & 63]), Tl = f2(tabl[kx & 63], tabl[ky & 63]);
+  const float2 ph = mul2(Th, E.h);
+  const float2 pl = fma2(Th, E.h, neg2(ph));
+  const ff2 s2 = two_sum2(Th, ph);
+  const float2 low = add2(add2(s2.l, pl), fma2(Th, E.l, fma2(Tl, E.h, Tl)));
+  const ff2 res = fast_two_sum2(s2.h, low);
+  const float2 sc = f2(__int_as_float(((kx >> 6) + 127) << 23), __int_as_float(((ky >> 6) + 127) << 23));
+  ff2 out{mul2(res.h, sc), mul2(res.l, sc)};
+  if (a.h.x < -87.0f) out.h.x = out.l.x = 0.0f;
+  if (a.h.y < -87.0f) out.h.y = out.l.y = 0.0f;
+  return out;
 }
 
 __device__ __forceinline__ bool frac_better(double a, double da, int ra, double b, double db,
@@ -89,9 +97,30 @@ __device__ __forceinline__ bool frac_better(double a, double da, int ra, double 
   return l > r || (l == r && ra < rb);
 }
 
+// Screen score comparison: larger score, ties to the smaller rank.
+__device__ __forceinline__ void track2(float sc, int c, float &b1, int &r1, float &b2) {
+  if (sc > b1 || (sc == b1 && c < r1)) {
+    b2 = b1;
+    b1 = sc;
+    r1 = c;
+  } else if (sc > b2) {
+    b2 = sc;
+  }
+}
+
+__device__ __forceinline__ void merge2(float o1, int orr, float o2, float &b1, int &r1, float &b2) {
+  if (o1 > b1 || (o1 == b1 && orr < r1)) {
+    b2 = fmaxf(b1, o2);
+    b1 = o1;
+    r1 = orr;
+  } else {
+    b2 = fmaxf(b2, o1);
+  }
+}
+
 // Right-looking FP64 Cholesky of the j x j design matrix held in A (row-major, leading
 // dimension lda) together with naug extra columns (forward substitution of them).  The
-// matrix entries are built by the caller.  Returns false (in *fail) on a pivot <= 0.
+// matrix entries are built by the caller.  Sets *fail on a pivot <= 0.
 __device__ void chol_aug_fp64(double *A, int j, int lda, int naug, int *fail) {
   const int tid = threadIdx.x;
   for (int k = 0; k < j; k++) {
@@ -135,34 +164,36 @@ __device__ __forceinline__ double corr64(const double *a, const double *b, int p
 
 __global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int Mpad = P.Mpad, n = P.n, p = P.p, M = P.M;
-  ff *vff = reinterpret_cast<ff *>(smraw);       // Mpad
-  ff *cff = vff + Mpad;                          // Mpad
-  ff *srow = cff + Mpad;                         // n
-  int *dr = reinterpret_cast<int *>(srow + n);   // n: ranks of the design, in order
-  int *rlist = dr + n;                           // RESCORE_CAP
+  const int Qpad = P.Qpad, n = P.n, p = P.p, M = P.M;
+  float4 *vp = reinterpret_cast<float4 *>(smraw);            // Qpad: v_j(c) pairs
+  float4 *cp = vp + Qpad;                                    // Qpad: cov_j(x, c) pairs
+  float2 *wrow = reinterpret_cast<float2 *>(cp + Qpad);      // (MB/32) x (n + kMaxP): per-warp s row
+  int *dr = reinterpret_cast<int *>(wrow + (MB / 32) * (n + kMaxP));  // n
+  int *rlist = dr + n;                                       // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
   __shared__ double xl[kMaxP];
-  __shared__ ff xs[kMaxP];
-  __shared__ float red_s1[MB / 32], red_s2[MB / 32];
-  __shared__ int red_r1[MB / 32];
+  __shared__ float red_s1[2][MB / 32], red_s2[2][MB / 32];
+  __shared__ int red_r1[2][MB / 32];
   __shared__ double red_n[MB / 32], red_d[MB / 32];
-  __shared__ int sh_loc, sh_best, sh_fail, sh_near, sh_nlist;
-  __shared__ ff sh_inv, sh_uxj;
+  __shared__ int red_rr[MB / 32];
+  __shared__ int sh_loc, sh_fail, sh_nlist, sh_rbest;
   if (threadIdx.x < 64) {
     tabh[threadIdx.x] = c_exp.tabf_h[threadIdx.x];
     tabl[threadIdx.x] = c_exp.tabf_l[threadIdx.x];
     etab[threadIdx.x] = c_exp.tab[threadIdx.x];
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  ff *U = P.U + (size_t)blockIdx.x * n * Mpad;
-  ff *Xr = P.Xr + (size_t)blockIdx.x * p * Mpad;
+  float4 *U = P.U + (size_t)blockIdx.x * n * Qpad;
+  float4 *Xr = P.Xr + (size_t)blockIdx.x * p * Qpad;
   const int lda = n + 2;
   double *A = P.A + (size_t)blockIdx.x * n * lda;
+  float2 *srow = wrow + warp * (n + kMaxP);  // this warp's copy of the new factor row
+  float2 *sxs = srow + n;                    // and of the new point's coordinates
   const ff onepg = ff_from_double(P.onepg);
   const ff thinv = ff_from_double(P.theta_inv);
+  const int Q = (M + 1) >> 1;
 
   for (;;) {
     __syncthreads();
@@ -174,156 +205,165 @@ __global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
     if (tid < p) xl[tid] = P.XX[loc * p + tid];
     if (tid == 0) sh_fail = 0;
     __syncthreads();
-    // coordinates relative to x (float-float), v = 1+g, cov_0(x,c) = K(x,c) in FP64
-    for (int c = tid; c < M; c += MB) {
-      const double *xc = P.X + (int64_t)cnd[c] * p;
-      double acc = 0.0;
-      for (int k = 0; k < p; k++) {
-        const double dk = xc[k] - xl[k];
-        Xr[k * Mpad + c] = ff_from_double(dk);
-        acc = fma(dk, dk, acc);
+    // coordinates relative to x (float-float pairs), v = 1+g, cov_0(x,c) = K(x,c) in FP64
+    for (int q = tid; q < Qpad; q += MB) {
+      ff cv[2];
+      for (int h = 0; h < 2; h++) {
+        const int c = 2 * q + h;
+        cv[h] = ff{0.0f, 0.0f};
+        if (c < M) {
+          const double *xc = P.X + (int64_t)cnd[c] * p;
+          double acc = 0.0;
+          for (int k = 0; k < p; k++) {
+            const double dk = xc[k] - xl[k];
+            const ff fk = ff_from_double(dk);
+            float *slot = reinterpret_cast<float *>(Xr + k * Qpad + q);
+            slot[h] = fk.h;
+            slot[2 + h] = fk.l;
+            acc = fma(dk, dk, acc);
+          }
+          cv[h] = ff_from_double(exp_nonpos(-acc * P.theta_inv, etab));
+        } else {
+          for (int k = 0; k < p; k++) {
+            float *slot = reinterpret_cast<float *>(Xr + k * Qpad + q);
+            slot[h] = 0.0f;
+            slot[2 + h] = 0.0f;
+          }
+        }
+        used[c] = (c < M) ? 0 : 1;
       }
-      vff[c] = onepg;
-      cff[c] = ff_from_double(exp_nonpos(-acc * P.theta_inv, etab));
-      used[c] = 0;
+      vp[q] = make_float4(onepg.h, onepg.h, onepg.l, onepg.l);
+      cp[q] = make_float4(cv[0].h, cv[1].h, cv[0].l, cv[1].l);
     }
     __syncthreads();
 
+    int best = 0;
     for (int j = 0; j < n; j++) {
-      const int s = (j < P.n0) ? j : sh_best;
-      if (s < 0) {  // nothing admissible left (uniform across the block)
+      const int s = (j < P.n0) ? j : best;
+      if (s < 0) {  // nothing admissible left (the same for every thread)
         if (tid == 0) sh_fail = 1;
-        __syncthreads();
         break;
       }
-      if (tid == 0) {
-        const ff vs = vff[s];
-        if (!(vs.h > 0.0f)) {
-          sh_fail = 1;
-        } else {
-          dr[j] = s;
-          used[s] = 1;
-          const ff inv = ff_rcp(ff_sqrt(vs));
-          sh_inv = inv;
-          sh_uxj = ff_mul(cff[s], inv);
-        }
+      const ff vs = ff2_get(vp, s);
+      if (!(vs.h > 0.0f)) {
+        if (tid == 0) sh_fail = 1;
+        break;
       }
-      for (int i = tid; i < j; i += MB) srow[i] = U[(size_t)i * Mpad + s];
-      if (tid < p) xs[tid] = Xr[tid * Mpad + s];
-      __syncthreads();
-      if (sh_fail) break;
+      // every thread derives the step's scalars itself: no barrier needed for them
+      const ff inv = ff_rcp(ff_sqrt(vs));
+      const ff uxj = ff_mul(ff2_get(cp, s), inv);
+      if (tid == 0) dr[j] = s;
+      if (tid == ((s >> 1) % MB)) used[s] = 1;  // the pair's owner keeps the flags
+      // this warp's copy of the new factor row u_s and of x_s (relative to x)
+      for (int i = lane; i < j; i += 32) {
+        const ff u = ff2_get(U + (size_t)i * Qpad, s);
+        srow[i] = make_float2(u.h, u.l);
+      }
+      if (lane < p) {
+        const ff xk = ff2_get(Xr + lane * Qpad, s);
+        sxs[lane] = make_float2(xk.h, xk.l);
+      }
+      __syncwarp();
       if (j == n - 1) break;
-      const ff inv = sh_inv, uxj = sh_uxj;
       const bool want = j + 1 >= P.n0;
+      const ff2 inv2{f2s(inv.h), f2s(inv.l)}, uxj2{f2s(uxj.h), f2s(uxj.l)};
+      const ff2 thinv2{f2s(thinv.h), f2s(thinv.l)};
       float b1 = -1.0f, b2 = -1.0f;
       int r1 = 0x7fffffff;
-      for (int c = tid; c < M; c += MB) {
-        if (used[c]) continue;
-        // squared distance to the new point, from coordinates relative to x
-        float dh = 0.0f, dl = 0.0f;
+      for (int q = tid; q < Q; q += MB) {
+        const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+        if (u0 && u1) continue;
+        // squared distance of the pair to the new point
+        float2 dh = f2s(0.0f), dl = f2s(0.0f);
         for (int k = 0; k < p; k++) {
-          const ff a = xs[k], b = Xr[k * Mpad + c];
-          const ff df = two_sum(a.h, -b.h);
-          const float dfl = __fadd_rn(df.l, __fsub_rn(a.l, b.l));
-          const float ph = __fmul_rn(df.h, df.h);
-          const float pl = __fmaf_rn(2.0f * df.h, dfl, __fmaf_rn(df.h, df.h, -ph));
-          const ff sacc = two_sum(dh, ph);
+          const ff2 b = ff2_load(Xr + k * Qpad + q);
+          const float2 a = sxs[k];
+          const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
+          const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
+          const float2 ph = mul2(df.h, df.h);
+          const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
+          const ff2 sacc = two_sum2(dh, ph);
           dh = sacc.h;
-          dl = __fadd_rn(__fadd_rn(sacc.l, dl), pl);
+          dl = add2(add2(sacc.l, dl), pl);
         }
-        const ff d2 = fast_two_sum(dh, dl);
-        ff t = exp_ff(ff_neg(ff_mul(d2, thinv)), tabh, tabl);   // K(s, c)
-        const ff *Uc = U + c;
-        for (int i = 0; i < j; i++) t = ff_sub_prod_acc(t, srow[i], Uc[(size_t)i * Mpad]);
-        const ff u = ff_mul(t, inv);                              // u_c[j]
-        U[(size_t)j * Mpad + c] = u;
-        const ff v = ff_sub(vff[c], ff_mul(u, u));
-        const ff cx = ff_sub(cff[c], ff_mul(uxj, u));
-        vff[c] = v;
-        cff[c] = cx;
-        if (want && v.h > 0.0f) {
-          const float sc = __fdiv_rn(__fmul_rn(cx.h, cx.h), v.h);
-          if (sc > b1 || (sc == b1 && c < r1)) {
-            b2 = b1;
-            b1 = sc;
-            r1 = c;
-          } else if (sc > b2) {
-            b2 = sc;
-          }
+        const ff2 d2 = fast_two_sum2(dh, dl);
+        const ff2 arg = ff2_mul(d2, thinv2);
+        ff2 t = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, tabh, tabl);   // K(s, c)
+        const float4 *Uq = U + q;
+#pragma unroll 4
+        for (int i = 0; i < j; i++, Uq += Qpad) {
+          const float2 sr = srow[i];
+          const float4 uv = *Uq;
+          t = ff2_sub_prod_acc(t, f2s(sr.x), f2s(sr.y), make_float2(uv.x, uv.y),
+                               make_float2(uv.z, uv.w));
+        }
+        const ff2 u = ff2_mul(t, inv2);                            // u_c[j]
+        ff2_store(U + (size_t)j * Qpad + q, u);
+        const ff2 v0 = ff2_load(vp + q), c0 = ff2_load(cp + q);
+        ff2 v = ff2_sub(v0, ff2_mul(u, u));
+        ff2 cx = ff2_sub(c0, ff2_mul(uxj2, u));
+        // A used lane keeps its values: the step's pivot may be the partner of a live
+        // candidate, and other threads read the pivot's v and cov at the start of the
+        // step without a barrier after it.
+        if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
+        if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
+        ff2_store(vp + q, v);
+        ff2_store(cp + q, cx);
+        if (want) {
+          if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), 2 * q, b1, r1, b2);
+          if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), 2 * q + 1, b1, r1, b2);
         }
       }
-      if (!want) {
-        __syncthreads();
-        continue;
-      }
-      // best and second-best screen scores over the block
+      // best and second-best screen scores: warp shuffles, one barrier, then every
+      // thread merges the per-warp results itself (double-buffered by step parity)
+      const int par = j & 1;
       for (int o = 16; o > 0; o >>= 1) {
         const float ob1 = __shfl_down_sync(0xffffffffu, b1, o);
         const float ob2 = __shfl_down_sync(0xffffffffu, b2, o);
-        const int or1 = __shfl_down_sync(0xffffffffu, r1, o);
-        if (ob1 > b1 || (ob1 == b1 && or1 < r1)) {
-          b2 = fmaxf(b1, ob2);
-          b1 = ob1;
-          r1 = or1;
-        } else {
-          b2 = fmaxf(b2, ob1);
-        }
+        const int orr = __shfl_down_sync(0xffffffffu, r1, o);
+        merge2(ob1, orr, ob2, b1, r1, b2);
       }
       if (lane == 0) {
-        red_s1[warp] = b1;
-        red_s2[warp] = b2;
-        red_r1[warp] = r1;
+        red_s1[par][warp] = b1;
+        red_s2[par][warp] = b2;
+        red_r1[par][warp] = r1;
       }
       __syncthreads();
-      if (tid == 0) {
-        float B1 = red_s1[0], B2 = red_s2[0];
-        int R1 = red_r1[0];
-        for (int w = 1; w < MB / 32; w++) {
-          const float o1 = red_s1[w], o2 = red_s2[w];
-          const int orr = red_r1[w];
-          if (o1 > B1 || (o1 == B1 && orr < R1)) {
-            B2 = fmaxf(B1, o2);
-            B1 = o1;
-            R1 = orr;
-          } else {
-            B2 = fmaxf(B2, o1);
-          }
-        }
-        sh_best = (R1 == 0x7fffffff) ? -1 : R1;
-        sh_near = (R1 != 0x7fffffff && B2 >= B1 * (1.0f - DELTA)) ? 1 : 0;
-        sh_nlist = 0;
-      }
-      __syncthreads();
-      if (!sh_near) continue;
+      if (!want) continue;
+      float B1 = red_s1[par][0], B2 = red_s2[par][0];
+      int R1 = red_r1[par][0];
+      for (int w = 1; w < MB / 32; w++) merge2(red_s1[par][w], red_r1[par][w], red_s2[par][w], B1, R1, B2);
+      best = (R1 == 0x7fffffff) ? -1 : R1;
+      const bool near = R1 != 0x7fffffff && B2 >= B1 * (1.0f - DELTA);
+      if (!near) continue;
       // ---- FP64 re-score of the near-tied candidates (rare) ----
-      if (tid == 0 && P.rescores) atomicAdd(P.rescores, 1);
+      if (tid == 0) {
+        sh_nlist = 0;
+        if (P.rescores) atomicAdd(P.rescores, 1);
+      }
+      __syncthreads();
       const int jd = j + 1;  // design size now
-      const float Bbest = [&] {
-        const ff v = vff[sh_best], cx = cff[sh_best];
-        return __fdiv_rn(__fmul_rn(cx.h, cx.h), v.h);
-      }();
       for (int c = tid; c < M; c += MB) {
         if (used[c]) continue;
-        const ff v = vff[c], cx = cff[c];
+        const ff v = ff2_get(vp, c), cx = ff2_get(cp, c);
         if (!(v.h > 0.0f)) continue;
-        const float sc = __fdiv_rn(__fmul_rn(cx.h, cx.h), v.h);
-        if (sc >= Bbest * (1.0f - 2.0f * DELTA)) {
+        const float sc = __fdiv_rn(cx.h * cx.h, v.h);
+        if (sc >= B1 * (1.0f - 2.0f * DELTA)) {
           const int pos = atomicAdd(&sh_nlist, 1);
           if (pos < RESCORE_CAP) rlist[pos] = c;
         }
       }
-      // FP64 factor of the current design with k(x) as an extra column
-      for (int q = tid; q < jd * (jd + 1); q += MB) {
-        const int a = q / (jd + 1), b = q % (jd + 1);
+      // FP64 factor of the current design with k(x) as an extra column (lower triangle)
+      for (int qq = tid; qq < jd * (jd + 1); qq += MB) {
+        const int a = qq / (jd + 1), b = qq % (jd + 1);
+        if (b < jd && b > a) continue;
         const double *xa = P.X + (int64_t)cnd[dr[a]] * p;
-        if (b < jd && b > a) continue;  // only the lower triangle is read
         double val;
         if (b < jd) val = (a == b) ? P.onepg : corr64(xa, P.X + (int64_t)cnd[dr[b]] * p, p, P.theta_inv, etab);
         else val = corr64(xa, xl, p, P.theta_inv, etab);
         A[a * lda + b] = val;
       }
       __syncthreads();
-      // chol_aug_fp64 uses columns [0, jd) and jd as the augmented one (lda = n + 2 >= jd + 1)
       chol_aug_fp64(A, jd, lda, 1, &sh_fail);
       if (sh_fail) break;
       // more near-ties than the list holds: re-score every remaining candidate
@@ -370,25 +410,26 @@ __global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
       if (lane == 0) {
         red_n[warp] = bn;
         red_d[warp] = bd;
-        red_r1[warp] = br;
+        red_rr[warp] = br;
       }
       __syncthreads();
       if (tid == 0) {
         for (int w = 1; w < MB / 32; w++)
-          if (frac_better(red_n[w], red_d[w], red_r1[w], bn, bd, br)) {
+          if (frac_better(red_n[w], red_d[w], red_rr[w], bn, bd, br)) {
             bn = red_n[w];
             bd = red_d[w];
-            br = red_r1[w];
+            br = red_rr[w];
           }
-        if (br != 0x7fffffff) sh_best = br;
+        sh_rbest = (br != 0x7fffffff) ? br : best;
       }
       __syncthreads();
+      best = sh_rbest;
     }
     __syncthreads();
     if (!sh_fail) {
       // FP64 predictive equations on the final design: factor [K_n | k(x) | Y]
-      for (int q = tid; q < n * (n + 2); q += MB) {
-        const int a = q / (n + 2), b = q % (n + 2);
+      for (int qq = tid; qq < n * (n + 2); qq += MB) {
+        const int a = qq / (n + 2), b = qq % (n + 2);
         if (b < n && b > a) continue;  // only the lower triangle is read
         const double *xa = P.X + (int64_t)cnd[dr[a]] * p;
         double val;
@@ -433,11 +474,12 @@ int mix_grid(int64_t T, int num_sms) {
   return (int)(T < g ? (T > 0 ? T : 1) : g);
 }
 
-int mix_mpad(int M) { return (int)align_up((size_t)M, 32); }
+int mix_mpad(int M) { return (int)align_up((size_t)M, 64); }
 
 size_t mix_smem_bytes(int Mpad, int n) {
-  return (size_t)Mpad * 2 * sizeof(ff) + (size_t)n * sizeof(ff) + (size_t)n * sizeof(int) +
-         RESCORE_CAP * sizeof(int) + align_up((size_t)Mpad, 16);
+  const size_t Qpad = (size_t)Mpad / 2;
+  return Qpad * 2 * sizeof(float4) + (size_t)(MB / 32) * (n + kMaxP) * sizeof(float2) +
+         (size_t)n * sizeof(int) + RESCORE_CAP * sizeof(int) + align_up((size_t)Mpad, 16);
 }
 
 struct MixLayout {
@@ -445,10 +487,10 @@ struct MixLayout {
 };
 
 MixLayout mix_layout(int G, int p, int n, int M) {
-  const size_t Mpad = (size_t)mix_mpad(M);
+  const size_t Qpad = (size_t)mix_mpad(M) / 2;
   MixLayout L;
-  L.u = align_up((size_t)G * n * Mpad * sizeof(ff), 256);
-  L.xr = align_up((size_t)G * p * Mpad * sizeof(ff), 256);
+  L.u = align_up((size_t)G * n * Qpad * sizeof(float4), 256);
+  L.xr = align_up((size_t)G * p * Qpad * sizeof(float4), 256);
   L.a = align_up((size_t)G * n * (n + 2) * sizeof(double), 256);
   L.total = 256 + 256 + L.u + L.xr + L.a;
   return L;
@@ -473,13 +515,13 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   char *w = static_cast<char *>(ws);
   MixParams P;
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
-  P.M = a.M; P.Mpad = mix_mpad(a.M); P.n0 = a.n0; P.n = a.n;
+  P.M = a.M; P.Mpad = mix_mpad(a.M); P.Qpad = P.Mpad / 2; P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.rescores = reinterpret_cast<int *>(w + 256);
-  P.U = reinterpret_cast<ff *>(w + 512);
-  P.Xr = reinterpret_cast<ff *>(w + 512 + L.u);
+  P.U = reinterpret_cast<float4 *>(w + 512);
+  P.Xr = reinterpret_cast<float4 *>(w + 512 + L.u);
   P.A = reinterpret_cast<double *>(w + 512 + L.u + L.xr);
   const size_t smem = mix_smem_bytes(P.Mpad, a.n);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;

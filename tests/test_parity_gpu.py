@@ -208,3 +208,20 @@ def test_mixed_paper_2d_full_size_sampled_and_agrees_with_fp64():
     assert same.mean() >= 0.999, same.mean()
     rel = np.abs(f["s2"][same] - g["s2"][same]) / f["s2"][same]
     assert rel.max() <= 1e-9, rel.max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_repeated_runs_are_bitwise_identical(precision):
+    """Every location's arithmetic depends only on its own inputs: two runs (and the host
+    entry point) give bitwise-identical designs and values."""
+    w = inputs.paper_2d()
+    w.XX = np.ascontiguousarray(w.XX[:3000])
+    a = gpu_predict(w, precision=precision)
+    b = gpu_predict(w, precision=precision)
+    for k in ("idx", "mean", "s2", "var", "status"):
+        assert np.array_equal(a[k], b[k]), k
+    d = lagp.Design(w.X, w.Z)
+    h = d.predict(w.XX, w.n0, w.n, w.ncand, w.d, w.g, "alc", precision)
+    d.close()
+    for k in ("idx", "mean", "s2", "var", "status"):
+        assert np.array_equal(h[k], a[k]), k
