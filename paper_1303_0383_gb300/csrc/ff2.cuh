@@ -20,9 +20,11 @@ struct ff2 {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+// a - b as a packed fused multiply-add with multiplier -1: one rounding, the same result
+// as a subtraction, and no separate sign flips of the packed operands.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, f2s(-1.0f)); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -43,24 +45,30 @@ __device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b) {
   return fast_two_sum2(s.h, add2(s.l, add2(a.l, b.l)));
 }
 
-__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) { return ff2_add(a, ff2{neg2(b.h), neg2(b.l)}); }
-
-__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
-  const float2 p = mul2(a.h, b.h);
-  float2 e = fma2(a.h, b.h, neg2(p));
-  e = fma2(a.h, b.l, e);
-  e = fma2(a.l, b.h, e);
-  return fast_two_sum2(p, e);
+__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) {
+  const ff2 s = two_sum2(a.h, neg2(b.h));
+  return fast_two_sum2(s.h, add2(s.l, sub2(a.l, b.l)));
 }
 
-// acc - a*b with the same scalar multiplier a for both lanes (see ff_sub_prod_acc).
-__device__ __forceinline__ ff2 ff2_sub_prod_acc(ff2 acc, float2 ah, float2 al, float2 bh,
-                                                float2 bl) {
-  const float2 p = mul2(ah, bh);
-  float2 e = fma2(ah, bh, neg2(p));
+// TwoProd with the negated product formed directly: np = rn(-(a*b)) = -p, and
+// fma(a, b, np) = a*b - p exactly.
+__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
+  const float2 np = __fmul2_rn(__fmul2_rn(a.h, f2s(-1.0f)), b.h);
+  float2 e = fma2(a.h, b.h, np);
+  e = fma2(a.h, b.l, e);
+  e = fma2(a.l, b.h, e);
+  return fast_two_sum2(sub2(f2s(0.0f), np), e);
+}
+
+// acc - a*b with the same scalar multiplier a for both lanes (see ff_sub_prod_acc); the
+// caller passes a and its negation (nah = -a.h) so that no sign flip is needed per term.
+__device__ __forceinline__ ff2 ff2_sub_prod_acc(ff2 acc, float2 ah, float2 nah, float2 al,
+                                                float2 bh, float2 bl) {
+  const float2 np = mul2(nah, bh);        // -p
+  float2 e = fma2(ah, bh, np);            // a.h b.h - p
   e = fma2(ah, bl, e);
-  e = fma2(al, bh, e);
-  const ff2 s = two_sum2(acc.h, neg2(p));
+  e = fma2(al, bh, e);                    // a b - p (to float precision)
+  const ff2 s = two_sum2(acc.h, np);      // acc.h - p
   return fast_two_sum2(s.h, sub2(add2(s.l, acc.l), e));
 }
 

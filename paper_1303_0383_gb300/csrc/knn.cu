@@ -8,12 +8,11 @@
 // FP64 is 1/58 of FP32 throughput on this GPU, so exact distances are computed only for
 // the few points that can be members.  One CTA owns one location at a time:
 //   prep    (once per call) an FP32 copy of X and B = max |coordinate|;
-//   pass 1  FP32 squared distance d2f of every design point into the CTA's scratch row
-//           and a 4096-bin histogram of the top 12 bits of d2f (non-negative floats order
-//           like their bit patterns);
+//   pass 1  FP32 squared distance d2f of every design point and a 4096-bin histogram of
+//           the top 12 bits of d2f (non-negative floats order like their bit patterns);
 //   select  a block scan finds the bin b* holding the ncand-th smallest d2f; tau is the
 //           upper edge of b*;
-//   pass 2  every point with d2f <= tau + 2E survives, where E bounds |d2f - d2| (FP32
+//   pass 2  d2f recomputed (bit-identical); every point with d2f <= tau + 2E survives, where E bounds |d2f - d2| (FP32
 //           rounding of the coordinates, the differences and the fused sum; see
 //           fp32_err_bound) -- all true members survive; survivors get their exact FP64
 //           d2 and go to shared memory;
@@ -21,7 +20,7 @@
 //           are written out.
 // If the survivors do not fit in shared memory (many points tied at the boundary), the
 // CTA redoes that location exactly in FP64: a 4096-bin histogram of float(d2) over exact
-// d2 in scratch, and radix refinement on the 96-bit key (d2 bits, index) for an
+// d2 (recomputed in every pass: no scratch), and radix refinement on the 96-bit key (d2 bits, index) for an
 // oversized boundary bin.  Either way the result is bit-identical to a full sort.
 #include <float.h>
 
@@ -47,8 +46,11 @@ __device__ __forceinline__ uint32_t coarse_bin(double d2) {
   return __float_as_uint(__double2float_rn(d2)) >> (31 - HBITS);
 }
 
-__device__ __forceinline__ bool key_less(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib) {
-  return ka < kb || (ka == kb && ia < ib);
+// Keys are (d2 bits, index) compared as three 32-bit words (hi, lo, index): non-negative
+// doubles order like their bit patterns.
+__device__ __forceinline__ bool key_less3(uint32_t ah, uint32_t al, int32_t ai, uint32_t bh,
+                                          uint32_t bl, int32_t bi) {
+  return ah < bh || (ah == bh && (al < bl || (al == bl && ai < bi)));
 }
 
 // Digit d (0..11, most significant first) of the 96-bit key (bits:64 | index:32).
@@ -115,25 +117,35 @@ __device__ void find_rank_bin(const uint32_t *hist, int nbins, uint32_t rank, ui
   __syncthreads();
 }
 
-__device__ void bitonic_sort(uint64_t *key, int32_t *idx, int n2) {
+// Bitonic sort of n2 (a power of two) keys held as (hi, lo, index) words in shared memory;
+// each stage visits exactly its n2/2 compare-exchange pairs.
+__device__ void bitonic_sort(uint32_t *kh, uint32_t *kl, int32_t *idx, int n2) {
   for (int k = 2; k <= n2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += KB) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          uint64_t a = key[i], b = key[ixj];
-          int32_t ia = idx[i], ib = idx[ixj];
-          bool up = (i & k) == 0;
-          bool sw = up ? key_less(b, ib, a, ia) : key_less(a, ia, b, ib);
-          if (sw) {
-            key[i] = b; key[ixj] = a;
-            idx[i] = ib; idx[ixj] = ia;
-          }
+      const int lj = __ffs(j) - 1;
+      for (int pp = threadIdx.x; pp < (n2 >> 1); pp += KB) {
+        const int i = ((pp >> lj) << (lj + 1)) | (pp & (j - 1));
+        const int ixj = i + j;
+        const uint32_t ah = kh[i], al = kl[i], bh = kh[ixj], bl = kl[ixj];
+        const int32_t ai = idx[i], bi = idx[ixj];
+        const bool up = (i & k) == 0;
+        const bool sw = up ? key_less3(bh, bl, bi, ah, al, ai) : key_less3(ah, al, ai, bh, bl, bi);
+        if (sw) {
+          kh[i] = bh; kl[i] = bl; idx[i] = bi;
+          kh[ixj] = ah; kl[ixj] = al; idx[ixj] = ai;
         }
       }
       __syncthreads();
     }
   }
+}
+
+__device__ __forceinline__ void put_key(uint32_t *kh, uint32_t *kl, int32_t *sidx, uint32_t pos,
+                                        double d2, int32_t i) {
+  const uint64_t b = (uint64_t)__double_as_longlong(d2);
+  kh[pos] = (uint32_t)(b >> 32);
+  kl[pos] = (uint32_t)b;
+  sidx[pos] = i;
 }
 
 // Bound on |d2f - d2| for a squared distance d2 <= d computed in FP32 from coordinates
@@ -145,35 +157,29 @@ __device__ __forceinline__ double fp32_err_bound(double d, double B, int p) {
   return 8.0 * u * B * sqrt((double)p * d) + (4.0 + 2.0 * p) * u * d + 16.0 * p * u * u * B * B;
 }
 
-// Exact path for one location (also the fallback): FP64 d2 of every point in scratch D,
-// coarse histogram of float(d2), boundary resolution, keys into skey/sidx; returns count.
-__device__ int knn_exact_location(const double *__restrict__ X, int64_t N, int p, int M,
-                                  const double *xs, double *__restrict__ D, uint64_t *skey,
-                                  int32_t *sidx, uint32_t *hist, int cap, uint32_t *warp_tmp,
-                                  int *sh_bin, uint32_t *sh_below, uint32_t *sh_count,
-                                  uint32_t *pref) {
+// Exact path for one location (the fallback when many points tie at the boundary):
+// exact FP64 d2 of every point (recomputed in each pass, no scratch), coarse histogram of
+// float(d2), boundary resolution by radix refinement; keys into shared memory; returns
+// the count.
+__device__ int knn_exact_location(const double *__restrict__ X, int N, int p, int M,
+                                  const double *xs, uint32_t *kh, uint32_t *kl, int32_t *sidx,
+                                  uint32_t *hist, int cap, uint32_t *warp_tmp, int *sh_bin,
+                                  uint32_t *sh_below, uint32_t *sh_count, uint32_t *pref) {
   for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
   if (threadIdx.x == 0) *sh_count = 0;
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < N; i += KB) {
-    double d2 = sqdist_exact(xs, X + i * p, p);
-    D[i] = d2;
-    atomicAdd(&hist[coarse_bin(d2)], 1u);
-  }
+  for (int i = threadIdx.x; i < N; i += KB)
+    atomicAdd(&hist[coarse_bin(sqdist_exact(xs, X + (size_t)i * p, p))], 1u);
   __syncthreads();
   find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, sh_bin, sh_below);
   const uint32_t bstar = (uint32_t)*sh_bin;
   const uint32_t below = *sh_below;
   const uint32_t nb = hist[bstar];
   const bool fits = below + nb <= (uint32_t)cap;
-  for (int64_t i = threadIdx.x; i < N; i += KB) {
-    double d2 = D[i];
-    uint32_t b = coarse_bin(d2);
-    if (b < bstar || (fits && b == bstar)) {
-      uint32_t pos = atomicAdd(sh_count, 1u);
-      skey[pos] = (uint64_t)__double_as_longlong(d2);
-      sidx[pos] = (int32_t)i;
-    }
+  for (int i = threadIdx.x; i < N; i += KB) {
+    const double d2 = sqdist_exact(xs, X + (size_t)i * p, p);
+    const uint32_t b = coarse_bin(d2);
+    if (b < bstar || (fits && b == bstar)) put_key(kh, kl, sidx, atomicAdd(sh_count, 1u), d2, i);
   }
   __syncthreads();
   if (!fits) {
@@ -182,10 +188,10 @@ __device__ int knn_exact_location(const double *__restrict__ X, int64_t N, int p
     for (int d = 0; d < 12; d++) {
       for (int b = threadIdx.x; b < 256; b += KB) h256[b] = 0;
       __syncthreads();
-      for (int64_t i = threadIdx.x; i < N; i += KB) {
-        double d2 = D[i];
+      for (int i = threadIdx.x; i < N; i += KB) {
+        const double d2 = sqdist_exact(xs, X + (size_t)i * p, p);
         if (coarse_bin(d2) != bstar) continue;
-        uint64_t bits = (uint64_t)__double_as_longlong(d2);
+        const uint64_t bits = (uint64_t)__double_as_longlong(d2);
         if (!key_prefix_eq(bits, (uint32_t)i, d, pref)) continue;
         atomicAdd(&h256[key_digit(bits, (uint32_t)i, d)], 1u);
       }
@@ -194,17 +200,13 @@ __device__ int knn_exact_location(const double *__restrict__ X, int64_t N, int p
       find_rank_bin(h256, 256, need, warp_tmp, sh_bin, sh_below);
       const uint32_t dd = (uint32_t)*sh_bin, dbelow = *sh_below, deq = h256[dd];
       const bool last = cnt0 + dbelow + deq <= (uint32_t)cap;
-      for (int64_t i = threadIdx.x; i < N; i += KB) {
-        double d2 = D[i];
+      for (int i = threadIdx.x; i < N; i += KB) {
+        const double d2 = sqdist_exact(xs, X + (size_t)i * p, p);
         if (coarse_bin(d2) != bstar) continue;
-        uint64_t bits = (uint64_t)__double_as_longlong(d2);
+        const uint64_t bits = (uint64_t)__double_as_longlong(d2);
         if (!key_prefix_eq(bits, (uint32_t)i, d, pref)) continue;
-        uint32_t dg = key_digit(bits, (uint32_t)i, d);
-        if (dg < dd || (last && dg == dd)) {
-          uint32_t pos = atomicAdd(sh_count, 1u);
-          skey[pos] = bits;
-          sidx[pos] = (int32_t)i;
-        }
+        const uint32_t dg = key_digit(bits, (uint32_t)i, d);
+        if (dg < dd || (last && dg == dd)) put_key(kh, kl, sidx, atomicAdd(sh_count, 1u), d2, i);
       }
       __syncthreads();
       if (last) break;
@@ -235,17 +237,36 @@ __global__ void knn_prep_kernel(const double *__restrict__ X, int64_t n, float *
   }
 }
 
-__global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, int64_t N, int p,
+template <int P>
+__device__ __forceinline__ float sqdist_f32(const float *xf, const float *xi, int p) {
+  float acc = 0.0f;
+  if (P > 0) {
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      const float dk = __fsub_rn(xf[k], xi[k]);
+      acc = __fmaf_rn(dk, dk, acc);
+    }
+  } else {
+    for (int k = 0; k < p; k++) {
+      const float dk = __fsub_rn(xf[k], xi[k]);
+      acc = __fmaf_rn(dk, dk, acc);
+    }
+  }
+  return acc;
+}
+
+// P > 0: the dimension is a compile-time constant; P == 0: runtime p.
+template <int P>
+__global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, int N, int p,
                                                  const double *__restrict__ XX, int64_t T, int M,
                                                  int32_t *__restrict__ cand,
                                                  const float *__restrict__ Xf,
-                                                 const unsigned int *__restrict__ bmax,
-                                                 float *__restrict__ wsf, double *__restrict__ wsd,
-                                                 int cap) {
+                                                 const unsigned int *__restrict__ bmax, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t *skey = reinterpret_cast<uint64_t *>(smem);                 // cap
-  int32_t *sidx = reinterpret_cast<int32_t *>(skey + cap);             // cap
-  uint32_t *hist = reinterpret_cast<uint32_t *>(sidx + cap);           // HBINS
+  uint32_t *kh = reinterpret_cast<uint32_t *>(smem);   // cap
+  uint32_t *kl = kh + cap;                              // cap
+  int32_t *sidx = reinterpret_cast<int32_t *>(kl + cap);  // cap
+  uint32_t *hist = reinterpret_cast<uint32_t *>(sidx + cap);  // HBINS
   __shared__ double xs[kMaxP];
   __shared__ float xf[kMaxP];
   __shared__ uint32_t warp_tmp[32];
@@ -253,9 +274,8 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
   __shared__ uint32_t sh_below, sh_count;
   __shared__ uint32_t pref[12];
   __shared__ float sh_thr;
+  if (P > 0) p = P;
 
-  float *Df = wsf + (size_t)blockIdx.x * (size_t)N;
-  double *D = wsd + (size_t)blockIdx.x * (size_t)N;
   const double Bx = (double)__uint_as_float(*bmax);
   for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
     if (threadIdx.x < p) {
@@ -265,19 +285,10 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
     if (threadIdx.x == 0) sh_count = 0;
     __syncthreads();
-    // pass 1: FP32 distances and their histogram (32-bit indices: N < 2^31)
-    const int Ni = (int)N;
-    {
-      const float *xi = Xf + threadIdx.x * p;
-      for (int i = threadIdx.x; i < Ni; i += KB, xi += KB * p) {
-        float acc = 0.0f;
-        for (int k = 0; k < p; k++) {
-          const float dk = __fsub_rn(xf[k], xi[k]);
-          acc = __fmaf_rn(dk, dk, acc);
-        }
-        Df[i] = acc;
-        atomicAdd(&hist[__float_as_uint(acc) >> (31 - HBITS)], 1u);
-      }
+    // pass 1: histogram of the FP32 distances
+    for (int i = threadIdx.x; i < N; i += KB) {
+      const float d2f = sqdist_f32<P>(xf, Xf + (size_t)i * p, p);
+      atomicAdd(&hist[__float_as_uint(d2f) >> (31 - HBITS)], 1u);
     }
     __syncthreads();
     find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, &sh_bin, &sh_below);
@@ -291,31 +302,30 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     }
     __syncthreads();
     const float thr = sh_thr;
-    // pass 2: survivors get exact FP64 distances
-    for (int i = threadIdx.x; i < Ni; i += KB) {
-      if (Df[i] <= thr) {
+    // pass 2: the same FP32 distances again (bit for bit); survivors get exact FP64 ones
+    for (int i = threadIdx.x; i < N; i += KB) {
+      const float d2f = sqdist_f32<P>(xf, Xf + (size_t)i * p, p);
+      if (d2f <= thr) {
         const double d2 = sqdist_exact(xs, X + (size_t)i * p, p);
         const uint32_t pos = atomicAdd(&sh_count, 1u);
-        if (pos < (uint32_t)cap) {
-          skey[pos] = (uint64_t)__double_as_longlong(d2);
-          sidx[pos] = (int32_t)i;
-        }
+        if (pos < (uint32_t)cap) put_key(kh, kl, sidx, pos, d2, i);
       }
     }
     __syncthreads();
     int cnt = (int)sh_count;
     __syncthreads();
     if (cnt > cap || cnt < M)  // too many ties at the boundary (or, defensively, too few)
-      cnt = knn_exact_location(X, N, p, M, xs, D, skey, sidx, hist, cap, warp_tmp, &sh_bin,
+      cnt = knn_exact_location(X, N, p, M, xs, kh, kl, sidx, hist, cap, warp_tmp, &sh_bin,
                                &sh_below, &sh_count, pref);
     int n2 = 1;
     while (n2 < cnt) n2 <<= 1;
     for (int i = cnt + threadIdx.x; i < n2; i += KB) {
-      skey[i] = ~0ull;
+      kh[i] = 0xffffffffu;
+      kl[i] = 0xffffffffu;
       sidx[i] = 0x7fffffff;
     }
     __syncthreads();
-    bitonic_sort(skey, sidx, n2);
+    bitonic_sort(kh, kl, sidx, n2);
     for (int r = threadIdx.x; r < M; r += KB) cand[t * M + r] = sidx[r];
     __syncthreads();
   }
@@ -327,21 +337,24 @@ int knn_cap(int M) {
   return cap;
 }
 
-size_t knn_smem_bytes(int cap) { return (size_t)cap * (8 + 4) + HBINS * 4; }
+size_t knn_smem_bytes(int cap) { return (size_t)cap * (4 + 4 + 4) + HBINS * 4; }
 
-int knn_grid(int64_t T, int num_sms) {
-  int64_t g = (int64_t)num_sms * 2;
+int knn_grid(int64_t T, int num_sms, size_t smem) {
+  int per_sm = (int)(200000 / (smem + 1024));  // leave room, at most 8 CTAs of 256 threads
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  const int64_t g = (int64_t)num_sms * per_sm;
   return (int)(T < g ? (T > 0 ? T : 1) : g);
 }
 
 }  // namespace
 
-// Scratch layout: [bmax (256 B)] [Xf: N*p floats] [per CTA: N floats] [per CTA: N doubles]
+// Scratch layout: [bmax (256 B)] [Xf: N*p floats]
 size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms) {
+  (void)T;
   (void)ncand;
-  const size_t G = (size_t)knn_grid(T, num_sms);
-  return 256 + align_up((size_t)N * kMaxP * sizeof(float), 256) +
-         align_up(G * (size_t)N * sizeof(float), 256) + align_up(G * (size_t)N * sizeof(double), 256);
+  (void)num_sms;
+  return 256 + align_up((size_t)N * kMaxP * sizeof(float), 256);
 }
 
 int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
@@ -354,16 +367,21 @@ int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t 
   const int cap = knn_cap(ncand);
   const size_t smem = knn_smem_bytes(cap);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const void *fn;
+  switch (p) {
+    case 1: fn = (const void *)knn_kernel<1>; break;
+    case 2: fn = (const void *)knn_kernel<2>; break;
+    case 3: fn = (const void *)knn_kernel<3>; break;
+    case 4: fn = (const void *)knn_kernel<4>; break;
+    case 8: fn = (const void *)knn_kernel<8>; break;
+    default: fn = (const void *)knn_kernel<0>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
-  const int grid = knn_grid(T, di.num_sms);
+  const int grid = knn_grid(T, di.num_sms, smem);
   char *w = static_cast<char *>(ws);
   unsigned int *bmax = reinterpret_cast<unsigned int *>(w);
   float *Xf = reinterpret_cast<float *>(w + 256);
-  float *wsf = reinterpret_cast<float *>(w + 256 + align_up((size_t)N * kMaxP * sizeof(float), 256));
-  double *wsd = reinterpret_cast<double *>(reinterpret_cast<char *>(wsf) +
-                                           align_up((size_t)grid * N * sizeof(float), 256));
   e = cudaMemsetAsync(bmax, 0, sizeof(unsigned int), stream);
   if (e != cudaSuccess) return cuda_status(e);
   const int64_t n = N * p;
@@ -371,7 +389,11 @@ int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t 
   if (pblocks > 4 * di.num_sms) pblocks = 4 * di.num_sms;
   knn_prep_kernel<<<pblocks, KB, 0, stream>>>(X, n, Xf, bmax);
   g_launches.fetch_add(1);
-  knn_kernel<<<grid, KB, smem, stream>>>(X, N, p, XX, T, ncand, cand, Xf, bmax, wsf, wsd, cap);
+  const int Ni = (int)N;
+  void *args[] = {(void *)&X, (void *)&Ni, (void *)&p, (void *)&XX, (void *)&T, (void *)&ncand,
+                  (void *)&cand, (void *)&Xf, (void *)&bmax, (void *)&cap};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(KB), args, smem, stream);
+  if (e != cudaSuccess) return cuda_status(e);
   g_launches.fetch_add(1);
   return cuda_status(cudaGetLastError());
 }

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
         for (int i = 0; i < j; i++, Uq += Qpad) {
           const float2 sr = srow[i];
           const float4 uv = *Uq;
-          t = ff2_sub_prod_acc(t, f2s(sr.x), f2s(sr.y), make_float2(uv.x, uv.y),
+          t = ff2_sub_prod_acc(t, f2s(sr.x), f2s(-sr.x), f2s(sr.y), make_float2(uv.x, uv.y),
                                make_float2(uv.z, uv.w));
         }
         const ff2 u = ff2_mul(t, inv2);                            // u_c[j]
