@@ -7,10 +7,12 @@ over [-1.97,1.97]^2, lengthscale d=0.5, nugget g=1e-6, n0=6 -> n=50 by ALC over 
 1000 nearest candidates.  One step = the whole path for all 10000 locations: kernel (a)
 (candidate sets) then kernels (b)+(c) (greedy design + predictive equations).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|fp64|mixed]
   python bench.py --impl reference ...   # the CPU oracle on host cores (a baseline)
 
-Prints one JSON line.  Under torchrun every rank runs the full workload on its own GPU
+The headline value is the mixed-precision path (float-float screen, FP64 decisions and
+predictions); the plain FP64 path is timed in the same run and reported under
+"variants".  Prints one JSON line.  Under torchrun every rank runs the full workload on its own GPU
 (independent problems, no collective on the data path: weak scaling); `value` is all
 ranks' predictions over the slowest rank's time.
 """
@@ -61,6 +63,22 @@ def select_flops_per_location(n0, n, M, p, method="alc"):
     for j in range(n - 1):
         pool = M - (j + 1)
         total += pool * (2 * j + 3 * p + 1 + EXP_FLOPS + 7)
+    return float(total)
+
+
+FP32_PEAK_TOPS_DERIVED = 152 * 128 * 2.07e9 / 1e12   # SMs x FP32 lanes/clk x max clock
+
+
+def mixed_fp32_ops_per_location(n0, n, M, p):
+    """FP32 operations (add, multiply or fused multiply-add, each one) of the float-float
+    screen for one location: every pool candidate at step j costs 15j (the float-float
+    row dot: TwoProd with cross terms, TwoSum, renormalisation) + 20p + 3 (squared
+    distance) + 11 (scaling by 1/theta) + 66 (float-float exponential) + 9 (new row entry)
+    + 42 (v and cov updates) + 6 (screen score)."""
+    total = 0
+    for j in range(n - 1):
+        pool = M - (j + 1)
+        total += pool * (15 * j + 20 * p + 3 + 11 + 66 + 9 + 42 + 6)
     return float(total)
 
 
@@ -194,27 +212,12 @@ def e2e_timing(args, w, M, method, prec, flush, idx_dev):
     return 1e3 * sum(times) / len(times)
 
 
-def run_gpu(args):
-    import torch
-    rank, world, local = env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = torch.device("cuda", torch.cuda.current_device())
-    from paper_1303_0383_gb300 import inputs, lagp
-    lagp.load()
-    w = inputs.paper_2d()
-    if args.locations:
-        w.XX = np.ascontiguousarray(w.XX[: args.locations])
-        w.name += " (first %d locations)" % args.locations
-    method, prec = "alc", args.precision
-    stream = torch.cuda.current_stream()
-
-    X = torch.as_tensor(w.X).to(dev)
-    Z = torch.as_tensor(w.Z).to(dev)
-    XX = torch.as_tensor(w.XX).to(dev)
+def time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch):
+    """Warm up, then time args.steps steps of kernel (a) + kernels (b)+(c) with CUDA events
+    per kernel on the launching stream (L2 flushed between steps, outside the events)."""
+    dev = X.device
     T, M = w.T, w.ncand
+    method = "alc"
     cand = torch.empty((T, M), dtype=torch.int32, device=dev)
     mean = torch.empty(T, dtype=torch.float64, device=dev)
     s2, var = torch.empty_like(mean), torch.empty_like(mean)
@@ -222,7 +225,6 @@ def run_gpu(args):
     status = torch.empty(T, dtype=torch.int8, device=dev)
     ws_knn = lagp.workspace(lagp.lagp_knn_workspace_bytes(w.N, T, M), dev)
     ws_sel = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, w.n, M, method, prec), dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
     def step(evs=None):
         if evs:
@@ -239,89 +241,144 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
     assert int((status != 0).sum()) == 0, "failed locations in warm-up"
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
-    sampler.start()
     launches0 = lagp.lagp_launch_count()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    barrier()
+    barrier(torch)
     for k in range(args.steps):
         flush.add_(1.0)                 # evict L2 between timed steps (not timed)
         step(evs[k])
-    barrier()
+    barrier(torch)
     launches = lagp.lagp_launch_count() - launches0
     knn_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sel_ms = [e[1].elapsed_time(e[2]) for e in evs]
     step_ms = [a + b for a, b in zip(knn_ms, sel_ms)]
-    ms_local = sum(step_ms) / len(step_ms)
-
-    # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
-    e2e_ms_local = float("nan")
-    if not args.no_e2e:
-        e2e_ms_local = e2e_timing(args, w, M, method, prec, flush, idx)
-    clocks = sampler.stop()
+    return dict(ms=sum(step_ms) / len(step_ms), knn_ms=sum(knn_ms) / len(knn_ms),
+                sel_ms=sum(sel_ms) / len(sel_ms), launches=int(launches), idx=idx)
 
 
+def barrier(torch):
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+
+def roofline_for(prec, w, sel_ms, traffic):
+    T, M = w.T, w.ncand
+    if prec == "fp64":
+        work = select_flops_per_location(w.n0, w.n, M, w.p)
+        achieved = work * T / (sel_ms / 1e3) / 1e12
+        return {"kernel": "select_fp64_kernel (kernels b+c)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "traffic": traffic,
+                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "work_per_location": work, "work_unit": "FP64 flops (FMA = 2, exp = 20)"}
+    work = mixed_fp32_ops_per_location(w.n0, w.n, M, w.p)
+    achieved = work * T / (sel_ms / 1e3) / 1e12
+    return {"kernel": "select_mixed_kernel (kernels b+c)", "bound": "alu", "achieved": achieved,
+            "peak": FP32_PEAK_TOPS_DERIVED, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TOPS_DERIVED,
+            "traffic": traffic,
+            "peak_source": "derived FP32: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane-cycle)",
+            "work_per_location": work,
+            "work_unit": "FP32 operations of the float-float screen (add, mul or FMA = 1)"}
+
+
+def stored_traffic(prec):
+    tpath = os.path.join(ROOT, "profiles", "select_traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    try:
+        for tj in json.load(open(tpath)).get("entries", []):
+            if tj.get("precision") == prec and tj.get("source_sha256") == kernel_source_hash():
+                return tj.get("bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = env_rank()
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([ms_local, e2e_ms_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(tt[0]), float(tt[1])
-    else:
-        ms, e2e_ms = ms_local, e2e_ms_local
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1303_0383_gb300 import inputs, lagp
+    lagp.load()
+    w = inputs.paper_2d()
+    if args.locations:
+        w.XX = np.ascontiguousarray(w.XX[: args.locations])
+        w.name += " (first %d locations)" % args.locations
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    head = "mixed" if "mixed" in precs else precs[0]
+    stream = torch.cuda.current_stream()
+    X = torch.as_tensor(w.X).to(dev)
+    Z = torch.as_tensor(w.Z).to(dev)
+    XX = torch.as_tensor(w.XX).to(dev)
+    T = w.T
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    sampler.start()
+    res = {}
+    for prec in precs:
+        res[prec] = time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch)
+        # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
+        res[prec]["e2e_ms"] = float("nan") if args.no_e2e else \
+            e2e_timing(args, w, w.ncand, "alc", prec, flush, res[prec]["idx"])
+    clocks = sampler.stop()
+
+    for prec in precs:
+        r = res[prec]
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([r["ms"], r["e2e_ms"], r["sel_ms"]], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            r["ms"], r["e2e_ms"], r["sel_ms"] = float(tt[0]), float(tt[1]), float(tt[2])
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
 
-    value = world * T / (ms / 1e3)
-    sel_avg = sum(sel_ms) / len(sel_ms)
-    flops_loc = select_flops_per_location(w.n0, w.n, M, w.p)
-    achieved = flops_loc * T / (sel_avg / 1e3) / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "select_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            if tj.get("precision") == prec and tj.get("source_sha256") == kernel_source_hash():
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
-    cpu_val, cores, cpu_dt = (None, None, 0.0) if args.no_cpu else \
-        cpu_oracle_sample(w, min(args.cpu_sample, T))
     h2d = T * w.p * 8
     d2h = T * (8 * 3 + 4 * w.n + 1)
+    variants = {}
+    for prec in precs:
+        r = res[prec]
+        variants[prec] = {
+            "value": world * T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
+            "kernels_ms": {"knn": r["knn_ms"], "select": r["sel_ms"]},
+            "e2e": {"value": world * T / (r["e2e_ms"] / 1e3) if r["e2e_ms"] == r["e2e_ms"] else None,
+                    "ms_per_step": r["e2e_ms"]},
+            "gpu_launches": r["launches"],
+            "roofline": roofline_for(prec, w, r["sel_ms"], stored_traffic(prec)),
+        }
+    H = res[head]
+    cpu_val, cores, cpu_dt = (None, None, 0.0) if args.no_cpu else \
+        cpu_oracle_sample(w, min(args.cpu_sample, T))
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
+        "metric": METRIC, "value": variants[head]["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "f32x2+f64",
         "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "p": w.p, "T": w.T, "n0": w.n0, "n": w.n,
-                   "ncand": M, "d": w.d, "g": w.g, "method": method, "precision": prec,
+                   "ncand": w.ncand, "d": w.d, "g": w.g, "method": "alc", "precision": head,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas only: each GPU runs the whole workload"},
         "clocks": clocks,
-        "e2e": {"value": world * T / (e2e_ms / 1e3) if e2e_ms == e2e_ms else None, "unit": UNIT,
-                "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        "e2e": {"value": variants[head]["e2e"]["value"], "unit": UNIT,
+                "ms_per_step": H["e2e_ms"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "lagp_predict (host buffers, pinned)"},
-        "gpu_launches": int(launches),
-        "kernels_ms": {"knn": sum(knn_ms) / len(knn_ms), "select": sel_avg},
-        "roofline": {"kernel": "select (kernels b+c)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "traffic": traffic,
-                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                     "flops_per_location": flops_loc,
-                     "paper_form_effective_tflops":
-                         paper_form_flops_per_location(w.n0, w.n, M) * T / (sel_avg / 1e3) / 1e12},
+        "gpu_launches": H["launches"],
+        "kernels_ms": variants[head]["kernels_ms"],
+        "roofline": variants[head]["roofline"],
+        "variants": variants,
+        "paper_form_effective_tflops": {
+            prec: paper_form_flops_per_location(w.n0, w.n, w.ncand) * T / (res[prec]["sel_ms"] / 1e3) / 1e12
+            for prec in precs},
         "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d seeded locations of the %d (%.1f s wall)" %
                                    (min(args.cpu_sample, T), w.T, cpu_dt)},
@@ -339,7 +396,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--cpu-sample", type=int, default=480)
     ap.add_argument("--ref-sample", type=int, default=160)
     ap.add_argument("--locations", type=int, default=0,

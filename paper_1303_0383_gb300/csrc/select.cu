@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
     if (tid == 0) { sh_fail = 0; sh_vx = P.onepg; sh_psi = 0.0; }
     __syncthreads();
     // Stage candidate coordinates; v = K(c,c) = 1+g, cov_0(x,c) = K(x,c).
-    const int limit = (P.method == LAGP_NN) ? n : M;  // NN never looks past rank n-1
+    // NN, and ALC without greedy steps (n0 == n), never look past rank n-1
+    const int limit = (P.method == LAGP_NN || P.n0 == n) ? n : M;
     for (int c = tid; c < limit; c += SB) {
       const double *xc = P.X + (int64_t)cnd[c] * p;
       double acc = 0.0;

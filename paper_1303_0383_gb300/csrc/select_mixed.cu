@@ -162,7 +162,10 @@ __device__ __forceinline__ double corr64(const double *a, const double *b, int p
   return exp_nonpos(-acc * theta_inv, etab);
 }
 
-__global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
+#ifndef LAGP_MIX_MINB
+#define LAGP_MIX_MINB 3  // CTAs per SM: 85 registers per thread, no spills
+#endif
+__global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, n = P.n, p = P.p, M = P.M;
   float4 *vp = reinterpret_cast<float4 *>(smraw);            // Qpad: v_j(c) pairs
@@ -193,7 +196,8 @@ __global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
   float2 *sxs = srow + n;                    // and of the new point's coordinates
   const ff onepg = ff_from_double(P.onepg);
   const ff thinv = ff_from_double(P.theta_inv);
-  const int Q = (M + 1) >> 1;
+  // Without greedy steps (n0 == n) only the start design's own rows are ever read.
+  const int Q = ((P.n0 == P.n ? n : M) + 1) >> 1;
 
   for (;;) {
     __syncthreads();
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(MB, 2) select_mixed_kernel(MixParams P) {
 }
 
 int mix_grid(int64_t T, int num_sms) {
-  int64_t g = (int64_t)num_sms * 2;
+  int64_t g = (int64_t)num_sms * LAGP_MIX_MINB;
   return (int)(T < g ? (T > 0 ? T : 1) : g);
 }
 
