@@ -65,8 +65,10 @@ extern "C" {
 typedef enum { LAGP_ALC = 0, LAGP_MSPE = 1, LAGP_NN = 2 } lagp_method;
 
 /* LAGP_FP64: every step in FP64.
- * LAGP_MIXED: candidate screening in FP32, decisions and all updates in FP64 (the FP64
- * re-score of the leading candidates decides each greedy step). */
+ * LAGP_MIXED: the ALC candidate screen runs in float-float (pairs of FP32, about 48
+ * significant bits) on the FP32 pipes; near-tied decisions are re-scored in FP64 and the
+ * predictive equations are evaluated in FP64 on the final design.  MSPE runs in FP64 only
+ * (LAGP_MIXED with LAGP_MSPE returns LAGP_ERR_UNSUPPORTED); NN has no screen. */
 typedef enum { LAGP_FP64 = 0, LAGP_MIXED = 1 } lagp_precision;
 
 /* Human-readable name of a return code; never NULL, static storage. */
@@ -161,8 +163,8 @@ int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, con
  *     use fewer SMs (and take longer) than lagp_select_dev; results are identical.
  *   - A problem whose single CTA slot, 256 + (n + p) x ceil32(ncand) x 8 bytes (each
  *     part rounded up to 256), exceeds the array returns LAGP_ERR_SCRATCH_LIMIT.
- *   - Only the FP64 form runs here: precision LAGP_MIXED with ALC returns
- *     LAGP_ERR_UNSUPPORTED. */
+ *   - Only the FP64 ALC and NN forms run here: precision LAGP_MIXED with ALC, and the
+ *     MSPE method, return LAGP_ERR_UNSUPPORTED. */
 #define LAGP_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t N, int32_t p,

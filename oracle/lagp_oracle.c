@@ -37,8 +37,9 @@
  *   - the first n0 of the M nearest form D_{n0}; the other M-n0 are the search
  *     pool; the final design has exactly n points (n-n0 greedy steps).
  *   - ALC ties go to the smaller neighbour rank; MSPE ties likewise.
- *   - a pool member with v_j(c) <= 0 is skipped by the criterion; if the chosen
- *     point has v <= 0 the location fails with status LAGP_ORC_NOT_PD.
+ *   - a pool member with v_j(c) <= 0, or whose criterion evaluates to NaN (possible for
+ *     MSPE when the expected information is zero), is skipped by the criterion; if the
+ *     chosen point has v <= 0 the location fails with status LAGP_ORC_NOT_PD.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared.  Built a
  * second time with -DLAGP_ORACLE_LONG the same source computes in long double, an
@@ -514,6 +515,7 @@ static int local_design(const prob_t *P, work_t *W, const double *x, const int32
         }
       }
       if (c == forced_rank) forced_s = score;
+      if (score != score) continue;  /* a criterion that evaluates to NaN is not admissible */
       if (best < 0) {
         best = c; best_s = score;
       } else {

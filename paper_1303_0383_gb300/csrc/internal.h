@@ -61,6 +61,10 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
 size_t select_mixed_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
 int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+// MSPE variant of kernels (b)+(c), FP64.
+size_t select_mspe_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
+int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+
 // Argument checks shared by the entry points (api.cu).
 int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,
                  double theta, double g, int32_t method, int32_t precision);

@@ -53,7 +53,7 @@ extern "C" int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t
   if (st) return st;
   st = check_supported(method, precision);
   if (st) return st;
-  if (precision != LAGP_FP64 && method != LAGP_NN) return LAGP_ERR_UNSUPPORTED;
+  if (method == LAGP_MSPE || (precision != LAGP_FP64 && method != LAGP_NN)) return LAGP_ERR_UNSUPPORTED;
   if (T == 0) return LAGP_OK;
   if (!X || !Z || !XX || !cand || !mean || !s2) return LAGP_ERR_INVALID_ARG;
   const size_t cap = LAGP_NOALLOC_SCRATCH_BYTES;

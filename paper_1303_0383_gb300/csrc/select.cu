@@ -235,6 +235,7 @@ size_t sel_smem_bytes(int Mpad, int n) {
 
 size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
                               int32_t precision, int num_sms) {
+  if (method == LAGP_MSPE) return select_mspe_workspace_bytes(T, p, n, ncand, num_sms);
   if (precision == LAGP_MIXED && method == LAGP_ALC)
     return select_mixed_workspace_bytes(T, p, n, ncand, num_sms);
   const size_t Mpad = (size_t)mpad_of(ncand);
@@ -245,6 +246,7 @@ size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, in
 
 int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
   if (a.T == 0) return LAGP_OK;
+  if (a.method == LAGP_MSPE) return select_mspe_launch(a, ws, ws_bytes, stream);
   if (a.precision == LAGP_MIXED && a.method == LAGP_ALC)
     return select_mixed_launch(a, ws, ws_bytes, stream);
   DevInfo di;

@@ -225,3 +225,34 @@ def test_repeated_runs_are_bitwise_identical(precision):
     d.close()
     for k in ("idx", "mean", "s2", "var", "status"):
         assert np.array_equal(h[k], a[k]), k
+
+
+# ----------------------------------------------------------------- MSPE (FP64)
+
+def test_mspe_parity_tiny_2d():
+    w = inputs.tiny_2d()
+    g, infos, bad = run_parity(w, method="mspe")
+    assert not bad, bad[:3]
+
+
+@pytest.mark.parametrize("p,seed,g", [(1, 11, 1e-4), (2, 12, 1e-6), (3, 13, 1e-4), (8, 14, 1e-4)])
+def test_mspe_parity_random_small(p, seed, g):
+    w = inputs.random_case(200 + seed, 300, p, 19, 4, 18, 60, d=0.25 * p, g=g)
+    g_, infos, bad = run_parity(w, method="mspe")
+    assert not bad, bad[:3]
+
+
+def test_mspe_parity_smooth_8d_sample():
+    # the 8-d workload's shape (n0=8, n=100, 2000 candidates, g=1e-4) on a small sample
+    w = inputs.smooth_8d(T=24)
+    g, infos, bad = run_parity(w, locs=range(0, 24, 3), method="mspe")
+    assert not bad, bad[:3]
+
+
+def test_mspe_mixed_is_refused():
+    torch = _torch()
+    w = inputs.random_case(9, 300, 2, 4, 4, 15, 40)
+    X, Z, XX = dev(w.X, torch.float64), dev(w.Z, torch.float64), dev(w.XX, torch.float64)
+    with pytest.raises(lagp.LagpError) as e:
+        lagp.predict_torch(X, Z, XX, w.n0, w.n, w.ncand, w.d, w.g, "mspe", "mixed")
+    assert e.value.code == lagp.LAGP_ERR_UNSUPPORTED
