@@ -142,6 +142,49 @@ int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, con
                      int32_t *idx, int8_t *status, void *workspace, size_t workspace_bytes,
                      void *stream);
 
+/* ------------------------------------------------------------------ batched uneven problems */
+/* A batch mixes locations against several resident designs, each location with its own
+ * local design size n[t] and candidate count ncand[t] (the paper's knobs n and N', Secs.
+ * 3 and 6, chosen per location; Sec. 6 discusses spending effort unevenly).  Kernel (a)
+ * runs once per design over that design's locations and kernels (b)+(c) once over the
+ * whole batch, as one persistent launch over a queue ordered by estimated cost n^2 ncand
+ * (longest first).  Every location's results are bitwise the same as in a uniform call. */
+typedef struct {
+  const double *X;  /* N x p, device */
+  const double *Z;  /* N, device */
+  int64_t N;
+  int32_t p;        /* 1 .. 8 */
+  int32_t n0;       /* start-design size of every location on this design */
+  double theta;     /* lengthscale d */
+  double g;         /* nugget */
+} lagp_design_desc;
+
+/* flags of lagp_predict_batch_dev */
+#define LAGP_BATCH_TUNE 1u  /* first batch of a signature: time the launch shapes, keep the best */
+#define LAGP_BATCH_GRAPH 2u /* capture the launches in a CUDA graph once, replay afterwards */
+
+/* Scratch bytes lagp_predict_batch_dev needs (0 if the arguments are invalid).  The
+ * per-location arrays are host arrays of T entries. */
+size_t lagp_predict_batch_workspace_bytes(const lagp_design_desc *designs, int32_t ndesigns,
+                                          int64_t T, const int32_t *design_of, const int32_t *n,
+                                          const int32_t *ncand, int32_t method,
+                                          int32_t precision);
+
+/* The whole path for a batch (Secs. 3-4).  designs: host array of ndesigns descriptors
+ * (device X, Z).  XX: device, T rows of ldxx doubles (row t holds the location's p
+ * coordinates first).  design_of, n, ncand: host arrays (T each).  Rules per location:
+ * 3 <= n[t] <= 256, n[t] >= n0 of its design, n[t] <= ncand[t] <= min(N, 8192).
+ * Outputs (device): mean[T], s2[T] required; var[T], status[T] optional; idx, optional,
+ * holds sum(n) indices, location t's n[t] at offset n[0] + ... + n[t-1].
+ * flags: LAGP_BATCH_TUNE and/or LAGP_BATCH_GRAPH (see above; graphs are cached per
+ * signature and buffer set, and the per-location tables are copied in before each replay).
+ * The call enqueues on `stream`; with LAGP_BATCH_TUNE on a new signature it synchronises. */
+int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t ndesigns, const double *XX,
+                           int32_t ldxx, int64_t T, const int32_t *design_of, const int32_t *n,
+                           const int32_t *ncand, int32_t method, int32_t precision, double *mean,
+                           double *s2, double *var, int32_t *idx, int8_t *status, uint32_t flags,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ no-allocation variant */
 /* Kernels (b)+(c) as lagp_select_dev, for callers that cannot allocate device memory: a
  * plugin running inside a host application that owns every device allocation and forbids

@@ -14,6 +14,7 @@ namespace lagp {
 constexpr int kMaxP = 8;
 constexpr int kMaxN = 256;       // local design size n
 constexpr int kMaxCand = 8192;   // candidate count
+#define LAGP_MIX_CTAS_PER_SM 3     // resident CTAs per SM of the mixed kernel
 
 extern std::atomic<int64_t> g_launches;
 
@@ -32,6 +33,10 @@ int dev_info(DevInfo *out);
 size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms);
 int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
                int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream);
+struct LocDesc;
+int knn_launch_list(const double *X, int64_t N, int32_t p, const double *XX, int64_t nloc,
+                    int32_t M, int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream,
+                    const int32_t *list, const LocDesc *locs, int ldxx, int ctas_per_sm);
 
 // Kernels (b)+(c): greedy design and predictive equations.
 struct SelectArgs {
@@ -64,6 +69,36 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
 // MSPE variant of kernels (b)+(c), FP64.
 size_t select_mspe_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
 int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+// Batched launch of kernels (b)+(c): per-location tables in device memory (batch.cuh),
+// one persistent launch of G = ctas_per_sm x SMs CTAs over the cost-ordered queue.
+struct BatchDesign;
+struct BatchLaunch {
+  int32_t method, precision;
+  int64_t T;
+  const BatchDesign *designs;  // device
+  const LocDesc *locs;         // device, T entries
+  const int32_t *order;        // device, queue position -> location
+  const double *XX;
+  int32_t ldxx;
+  const int32_t *cand;         // device; location t's list at locs[t].cand_off
+  int32_t nmax, pmax, Mmax;
+  double *mean, *s2, *var;
+  int32_t *idx;                // location t's indices at locs[t].idx_off
+  int8_t *status;
+  int32_t ctas_per_sm;         // 1 .. select_max_ctas()
+};
+int select_max_ctas(int32_t method, int32_t precision);
+// Per-translation-unit set-up that must not happen during stream capture (constant uploads).
+int select_prepare();
+int select_mixed_prepare();
+int select_mspe_prepare();
+size_t select_batch_workspace_bytes(const BatchLaunch &b, int num_sms);
+int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t select_mixed_batch_workspace_bytes(const BatchLaunch &b, int G);
+int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G, cudaStream_t stream);
+size_t select_mspe_batch_workspace_bytes(const BatchLaunch &b, int G);
+int select_mspe_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G, cudaStream_t stream);
 
 // Argument checks shared by the entry points (api.cu).
 int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,

@@ -24,6 +24,7 @@
 // oversized boundary bin.  Either way the result is bit-identical to a full sort.
 #include <float.h>
 
+#include "batch.cuh"
 #include "internal.h"
 
 namespace lagp {
@@ -256,12 +257,17 @@ __device__ __forceinline__ float sqdist_f32(const float *xf, const float *xi, in
 }
 
 // P > 0: the dimension is a compile-time constant; P == 0: runtime p.
+// Batched launches pass `list` (launch position -> location), `locs` (each location's
+// candidate count and output offset) and the row stride of XX; uniform launches pass
+// nullptr and use M, t*M and t*p.
 template <int P>
 __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, int N, int p,
                                                  const double *__restrict__ XX, int64_t T, int M,
                                                  int32_t *__restrict__ cand,
                                                  const float *__restrict__ Xf,
-                                                 const unsigned int *__restrict__ bmax, int cap) {
+                                                 const unsigned int *__restrict__ bmax, int cap,
+                                                 const int32_t *__restrict__ list,
+                                                 const LocDesc *__restrict__ locs, int ldxx) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *kh = reinterpret_cast<uint32_t *>(smem);   // cap
   uint32_t *kl = kh + cap;                              // cap
@@ -277,9 +283,13 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
   if (P > 0) p = P;
 
   const double Bx = (double)__uint_as_float(*bmax);
-  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+  const int Mu = M;
+  for (int64_t tt = blockIdx.x; tt < T; tt += gridDim.x) {
+    const int64_t t = list ? list[tt] : tt;
+    int32_t *out = cand + (locs ? locs[t].cand_off : t * Mu);
+    M = locs ? locs[t].M : Mu;
     if (threadIdx.x < p) {
-      xs[threadIdx.x] = XX[t * p + threadIdx.x];
+      xs[threadIdx.x] = XX[t * (locs ? ldxx : p) + threadIdx.x];
       xf[threadIdx.x] = __double2float_rn(xs[threadIdx.x]);
     }
     for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     }
     __syncthreads();
     bitonic_sort(kh, kl, sidx, n2);
-    for (int r = threadIdx.x; r < M; r += KB) cand[t * M + r] = sidx[r];
+    for (int r = threadIdx.x; r < M; r += KB) out[r] = sidx[r];
     __syncthreads();
   }
 }
@@ -357,14 +367,18 @@ size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms) {
   return 256 + align_up((size_t)N * kMaxP * sizeof(float), 256);
 }
 
-int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
-               int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream) {
-  if (T == 0) return LAGP_OK;
+// Launch kernel (a) over nloc locations of one design.  Uniform launches: list == nullptr,
+// locs == nullptr, candidate count M.  Batched: the design's locations in list, their
+// counts and offsets in locs (M is then the largest count, which sizes shared memory).
+int knn_launch_list(const double *X, int64_t N, int32_t p, const double *XX, int64_t nloc,
+                    int32_t M, int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream,
+                    const int32_t *list, const LocDesc *locs, int ldxx, int ctas_per_sm) {
+  if (nloc == 0) return LAGP_OK;
   DevInfo di;
   int st = dev_info(&di);
   if (st) return st;
-  if (ws_bytes < knn_workspace_bytes(N, T, ncand, di.num_sms)) return LAGP_ERR_INVALID_ARG;
-  const int cap = knn_cap(ncand);
+  if (ws_bytes < knn_workspace_bytes(N, nloc, M, di.num_sms)) return LAGP_ERR_INVALID_ARG;
+  const int cap = knn_cap(M);
   const size_t smem = knn_smem_bytes(cap);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
   const void *fn;
@@ -378,7 +392,11 @@ int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t 
   }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
-  const int grid = knn_grid(T, di.num_sms, smem);
+  int grid = knn_grid(nloc, di.num_sms, smem);
+  if (ctas_per_sm > 0) {
+    const int64_t g2 = (int64_t)di.num_sms * ctas_per_sm;
+    grid = (int)(nloc < g2 ? nloc : g2);
+  }
   char *w = static_cast<char *>(ws);
   unsigned int *bmax = reinterpret_cast<unsigned int *>(w);
   float *Xf = reinterpret_cast<float *>(w + 256);
@@ -390,12 +408,18 @@ int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t 
   knn_prep_kernel<<<pblocks, KB, 0, stream>>>(X, n, Xf, bmax);
   g_launches.fetch_add(1);
   const int Ni = (int)N;
-  void *args[] = {(void *)&X, (void *)&Ni, (void *)&p, (void *)&XX, (void *)&T, (void *)&ncand,
-                  (void *)&cand, (void *)&Xf, (void *)&bmax, (void *)&cap};
+  void *args[] = {(void *)&X, (void *)&Ni, (void *)&p, (void *)&XX, (void *)&nloc, (void *)&M,
+                  (void *)&cand, (void *)&Xf, (void *)&bmax, (void *)&cap, (void *)&list,
+                  (void *)&locs, (void *)&ldxx};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(KB), args, smem, stream);
   if (e != cudaSuccess) return cuda_status(e);
   g_launches.fetch_add(1);
   return cuda_status(cudaGetLastError());
+}
+
+int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
+               int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  return knn_launch_list(X, N, p, XX, T, ncand, cand, ws, ws_bytes, stream, nullptr, nullptr, p, 0);
 }
 
 }  // namespace lagp

@@ -31,6 +31,7 @@
 // live in shared memory.
 #include <math.h>
 
+#include "batch.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -46,13 +47,15 @@ struct SelParams {
   int64_t T;
   const int32_t *cand;
   int M, Mpad, n0, n, method;
-  double theta_inv, onepg;
+  int nmax, pmax;  // slot dimensions (the largest n and p of the launch)
+  double theta, g;
   double *mean, *s2, *var;
   int32_t *idx;
   int8_t *status;
-  double *U;      // gridDim.x slots of n x Mpad
-  double *Xc;     // gridDim.x slots of p x Mpad
+  double *U;      // gridDim.x slots of nmax x Mpad
+  double *Xc;     // gridDim.x slots of pmax x Mpad
   int *queue;
+  BatchView B;    // per-location tables (B.designs == nullptr: uniform launch)
 };
 
 // ALC scores are compared as fractions cov^2 / v without dividing: a/da beats b/db when
@@ -65,13 +68,13 @@ __device__ __forceinline__ bool score_better(double a, double da, int ra, double
 
 __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
   extern __shared__ __align__(16) double sm[];
-  const int Mpad = P.Mpad, n = P.n, p = P.p, M = P.M;
+  const int Mpad = P.Mpad, nmax = P.nmax;
   double *v = sm;                       // Mpad
   double *covx = v + Mpad;              // Mpad
-  double *srow = covx + Mpad;           // n  (u_s, the new row of L)
-  double *ux = srow + n;                // n  (u_x = L^{-1} k(x))
-  double *yt = ux + n;                  // n  (ytil = L^{-1} Y)
-  unsigned char *used = reinterpret_cast<unsigned char *>(yt + n);  // Mpad
+  double *srow = covx + Mpad;           // nmax  (u_s, the new row of L)
+  double *ux = srow + nmax;             // nmax  (u_x = L^{-1} k(x))
+  double *yt = ux + nmax;               // nmax  (ytil = L^{-1} Y)
+  unsigned char *used = reinterpret_cast<unsigned char *>(yt + nmax);  // Mpad
   __shared__ double xs[kMaxP], xl[kMaxP];
   __shared__ double red_s[SB / 32], red_d[SB / 32];
   __shared__ int red_r[SB / 32];
@@ -81,24 +84,27 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
   __shared__ double sh_inv, sh_uxj, sh_vx, sh_psi;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double *U = P.U + (size_t)blockIdx.x * n * Mpad;
-  double *Xc = P.Xc + (size_t)blockIdx.x * p * Mpad;
+  double *U = P.U + (size_t)blockIdx.x * nmax * Mpad;
+  double *Xc = P.Xc + (size_t)blockIdx.x * P.pmax * Mpad;
 
   for (;;) {
     __syncthreads();
     if (tid == 0) sh_loc = atomicAdd(P.queue, 1);
     __syncthreads();
-    const int64_t loc = sh_loc;
-    if (loc >= P.T) break;
-    const int32_t *cnd = P.cand + loc * M;
-    if (tid < p) xl[tid] = P.XX[loc * p + tid];
-    if (tid == 0) { sh_fail = 0; sh_vx = P.onepg; sh_psi = 0.0; }
+    if (sh_loc >= P.T) break;
+    const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, P.M, P.n0, P.theta,
+                                    P.g, P.cand, P.idx);
+    const int64_t loc = L.loc;
+    const int n = L.n, p = L.p, M = L.M;
+    const int32_t *cnd = L.cand;
+    if (tid < p) xl[tid] = L.x[tid];
+    if (tid == 0) { sh_fail = 0; sh_vx = L.onepg; sh_psi = 0.0; }
     __syncthreads();
     // Stage candidate coordinates; v = K(c,c) = 1+g, cov_0(x,c) = K(x,c).
     // NN, and ALC without greedy steps (n0 == n), never look past rank n-1
-    const int limit = (P.method == LAGP_NN || P.n0 == n) ? n : M;
+    const int limit = (P.method == LAGP_NN || L.n0 == n) ? n : M;
     for (int c = tid; c < limit; c += SB) {
-      const double *xc = P.X + (int64_t)cnd[c] * p;
+      const double *xc = L.X + (int64_t)cnd[c] * p;
       double acc = 0.0;
       for (int k = 0; k < p; k++) {
         double xk = xc[k];
@@ -106,15 +112,15 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         double t = xl[k] - xk;
         acc = fma(t, t, acc);
       }
-      v[c] = P.onepg;
-      covx[c] = exp_nonpos(-acc * P.theta_inv, etab);
+      v[c] = L.onepg;
+      covx[c] = exp_nonpos(-acc * L.theta_inv, etab);
       used[c] = 0;
     }
     __syncthreads();
 
     int s = 0;
     for (int j = 0; j < n; j++) {
-      if (j >= P.n0 && P.method == LAGP_ALC) s = sh_best;
+      if (j >= L.n0 && P.method == LAGP_ALC) s = sh_best;
       else s = j;
       if (s < 0) {  // nothing admissible left
         if (tid == 0) sh_fail = 1;
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         } else {
           const double sq = sqrt(vs);
           const double uxj = covx[s] / sq;                 // u_x[j]
-          double t = P.Z[cnd[s]];
+          double t = L.Z[cnd[s]];
           for (int i = 0; i < j; i++) t = fma(-srow[i], yt[i], t);
           const double ytj = t / sq;                       // ytil[j]
           ux[j] = uxj;
@@ -141,14 +147,14 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
           sh_inv = 1.0 / sq;
           sh_uxj = uxj;
           used[s] = 1;
-          if (P.idx) P.idx[loc * n + j] = cnd[s];
+          if (L.idx) L.idx[j] = cnd[s];
         }
       }
       __syncthreads();
       if (sh_fail) break;
       if (j == n - 1) break;
       const double inv = sh_inv, uxj = sh_uxj;
-      const bool want_score = (P.method == LAGP_ALC) && (j + 1 >= P.n0);
+      const bool want_score = (P.method == LAGP_ALC) && (j + 1 >= L.n0);
       double bs = -1.0, bd = 1.0;   // best score as a fraction bs/bd (none yet: -1)
       int br = 0x7fffffff;
       for (int c = tid; c < limit; c += SB) {
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
           double t = xs[k] - Xc[k * Mpad + c];
           acc = fma(t, t, acc);
         }
-        double t = exp_nonpos(-acc * P.theta_inv, etab);  // K(s, c)
+        double t = exp_nonpos(-acc * L.theta_inv, etab);  // K(s, c)
         const double *Uc = U + c;
         for (int i = 0; i < j; i++, Uc += Mpad) t = fma(-srow[i], *Uc, t);
         const double u = t * inv;                          // u_c[j]
@@ -213,9 +219,9 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         if (P.status) P.status[loc] = 0;
       }
     }
-    if (sh_fail && P.idx) {
+    if (sh_fail && L.idx) {
       // A failed location reports no design: every index is -1.
-      for (int i = tid; i < n; i += SB) P.idx[loc * n + i] = -1;
+      for (int i = tid; i < n; i += SB) L.idx[i] = -1;
     }
   }
 }
@@ -262,8 +268,11 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   SelParams P;
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.method = a.method;
-  P.theta_inv = 1.0 / a.theta;
-  P.onepg = 1.0 + a.g;
+  P.theta = a.theta;
+  P.g = a.g;
+  P.nmax = a.n;
+  P.pmax = a.p;
+  P.B = BatchView{nullptr, nullptr, nullptr, 0};
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -303,8 +312,11 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   SelParams P;
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.method = a.method;
-  P.theta_inv = 1.0 / a.theta;
-  P.onepg = 1.0 + a.g;
+  P.theta = a.theta;
+  P.g = a.g;
+  P.nmax = a.n;
+  P.pmax = a.p;
+  P.B = BatchView{nullptr, nullptr, nullptr, 0};
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -320,5 +332,63 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   g_launches.fetch_add(1);
   return cuda_status(cudaGetLastError());
 }
+
+int select_max_ctas(int32_t method, int32_t precision) {
+  if (method == LAGP_MSPE) return 1;
+  if (precision == LAGP_MIXED && method == LAGP_ALC) return LAGP_MIX_CTAS_PER_SM;
+  return 2;
+}
+
+static int batch_grid(const BatchLaunch &b, int num_sms) {
+  int c = b.ctas_per_sm;
+  const int cmax = select_max_ctas(b.method, b.precision);
+  if (c < 1 || c > cmax) c = cmax;
+  const int64_t g = (int64_t)num_sms * c;
+  return (int)(b.T < g ? (b.T > 0 ? b.T : 1) : g);
+}
+
+size_t select_batch_workspace_bytes(const BatchLaunch &b, int num_sms) {
+  const int G = batch_grid(b, num_sms);
+  if (b.method == LAGP_MSPE) return select_mspe_batch_workspace_bytes(b, G);
+  if (b.precision == LAGP_MIXED && b.method == LAGP_ALC) return select_mixed_batch_workspace_bytes(b, G);
+  return select_scratch_bytes_for_grid(G, b.pmax, b.nmax, b.Mmax);
+}
+
+int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (b.T == 0) return LAGP_OK;
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st) return st;
+  st = exp_table_upload();
+  if (st) return st;
+  const int G = batch_grid(b, di.num_sms);
+  if (b.method == LAGP_MSPE) return select_mspe_batch_launch(b, ws, ws_bytes, G, stream);
+  if (b.precision == LAGP_MIXED && b.method == LAGP_ALC)
+    return select_mixed_batch_launch(b, ws, ws_bytes, G, stream);
+  if (ws_bytes < select_scratch_bytes_for_grid(G, b.pmax, b.nmax, b.Mmax)) return LAGP_ERR_INVALID_ARG;
+  const int Mpad = mpad_of(b.Mmax);
+  char *w = static_cast<char *>(ws);
+  SelParams P;
+  P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
+  P.M = b.Mmax; P.Mpad = Mpad; P.n0 = 0; P.n = b.nmax; P.method = b.method;
+  P.theta = 1.0; P.g = 0.0; P.nmax = b.nmax; P.pmax = b.pmax;
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx};
+  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
+  P.queue = reinterpret_cast<int *>(w);
+  P.U = reinterpret_cast<double *>(w + 256);
+  P.Xc = reinterpret_cast<double *>(w + 256 + align_up((size_t)G * b.nmax * Mpad * sizeof(double), 256));
+  const size_t smem = sel_smem_bytes(Mpad, b.nmax);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  select_fp64_kernel<<<G, SB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  return cuda_status(cudaGetLastError());
+}
+
+int select_prepare() { return exp_table_upload(); }
 
 }  // namespace lagp

@@ -28,6 +28,7 @@
 
 #include "ff.cuh"
 #include "ff2.cuh"
+#include "batch.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -45,7 +46,9 @@ struct MixParams {
   int64_t T;
   const int32_t *cand;
   int M, Mpad, Qpad, n0, n;
+  int nmax, pmax;  // slot dimensions (the largest n and p of the launch)
   double theta, theta_inv, g, onepg;
+  BatchView B;     // per-location tables (B.designs == nullptr: uniform launch)
   double *mean, *s2, *var;
   int32_t *idx;
   int8_t *status;
@@ -163,16 +166,16 @@ __device__ __forceinline__ double corr64(const double *a, const double *b, int p
 }
 
 #ifndef LAGP_MIX_MINB
-#define LAGP_MIX_MINB 3  // CTAs per SM: 85 registers per thread, no spills
+#define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM: 85 registers, no spills
 #endif
 __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int Qpad = P.Qpad, n = P.n, p = P.p, M = P.M;
+  const int Qpad = P.Qpad, nmax = P.nmax;
   float4 *vp = reinterpret_cast<float4 *>(smraw);            // Qpad: v_j(c) pairs
   float4 *cp = vp + Qpad;                                    // Qpad: cov_j(x, c) pairs
-  float2 *wrow = reinterpret_cast<float2 *>(cp + Qpad);      // (MB/32) x (n + kMaxP): per-warp s row
-  int *dr = reinterpret_cast<int *>(wrow + (MB / 32) * (n + kMaxP));  // n
-  int *rlist = dr + n;                                       // RESCORE_CAP
+  float2 *wrow = reinterpret_cast<float2 *>(cp + Qpad);      // (MB/32) x (nmax + kMaxP): per-warp s row
+  int *dr = reinterpret_cast<int *>(wrow + (MB / 32) * (nmax + kMaxP));  // nmax
+  int *rlist = dr + nmax;                                    // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
@@ -188,25 +191,28 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     etab[threadIdx.x] = c_exp.tab[threadIdx.x];
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float4 *U = P.U + (size_t)blockIdx.x * n * Qpad;
-  float4 *Xr = P.Xr + (size_t)blockIdx.x * p * Qpad;
-  const int lda = n + 2;
-  double *A = P.A + (size_t)blockIdx.x * n * lda;
-  float2 *srow = wrow + warp * (n + kMaxP);  // this warp's copy of the new factor row
-  float2 *sxs = srow + n;                    // and of the new point's coordinates
-  const ff onepg = ff_from_double(P.onepg);
-  const ff thinv = ff_from_double(P.theta_inv);
-  // Without greedy steps (n0 == n) only the start design's own rows are ever read.
-  const int Q = ((P.n0 == P.n ? n : M) + 1) >> 1;
+  float4 *U = P.U + (size_t)blockIdx.x * nmax * Qpad;
+  float4 *Xr = P.Xr + (size_t)blockIdx.x * P.pmax * Qpad;
+  const int lda = nmax + 2;
+  double *A = P.A + (size_t)blockIdx.x * nmax * lda;
+  float2 *srow = wrow + warp * (nmax + kMaxP);  // this warp's copy of the new factor row
+  float2 *sxs = srow + nmax;                    // and of the new point's coordinates
 
   for (;;) {
     __syncthreads();
     if (tid == 0) sh_loc = atomicAdd(P.queue, 1);
     __syncthreads();
-    const int64_t loc = sh_loc;
-    if (loc >= P.T) break;
-    const int32_t *cnd = P.cand + loc * M;
-    if (tid < p) xl[tid] = P.XX[loc * p + tid];
+    if (sh_loc >= P.T) break;
+    const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, P.M, P.n0, P.theta,
+                                    P.g, P.cand, P.idx);
+    const int64_t loc = L.loc;
+    const int n = L.n, p = L.p, M = L.M;
+    const int32_t *cnd = L.cand;
+    const ff onepg = ff_from_double(L.onepg);
+    const ff thinv = ff_from_double(L.theta_inv);
+    // Without greedy steps (n0 == n) only the start design's own rows are ever read.
+    const int Q = ((L.n0 == n ? n : M) + 1) >> 1;
+    if (tid < p) xl[tid] = L.x[tid];
     if (tid == 0) sh_fail = 0;
     __syncthreads();
     // coordinates relative to x (float-float pairs), v = 1+g, cov_0(x,c) = K(x,c) in FP64
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
         const int c = 2 * q + h;
         cv[h] = ff{0.0f, 0.0f};
         if (c < M) {
-          const double *xc = P.X + (int64_t)cnd[c] * p;
+          const double *xc = L.X + (int64_t)cnd[c] * p;
           double acc = 0.0;
           for (int k = 0; k < p; k++) {
             const double dk = xc[k] - xl[k];
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
             slot[2 + h] = fk.l;
             acc = fma(dk, dk, acc);
           }
-          cv[h] = ff_from_double(exp_nonpos(-acc * P.theta_inv, etab));
+          cv[h] = ff_from_double(exp_nonpos(-acc * L.theta_inv, etab));
         } else {
           for (int k = 0; k < p; k++) {
             float *slot = reinterpret_cast<float *>(Xr + k * Qpad + q);
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
 
     int best = 0;
     for (int j = 0; j < n; j++) {
-      const int s = (j < P.n0) ? j : best;
+      const int s = (j < L.n0) ? j : best;
       if (s < 0) {  // nothing admissible left (the same for every thread)
         if (tid == 0) sh_fail = 1;
         break;
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       }
       __syncwarp();
       if (j == n - 1) break;
-      const bool want = j + 1 >= P.n0;
+      const bool want = j + 1 >= L.n0;
       const ff2 inv2{f2s(inv.h), f2s(inv.l)}, uxj2{f2s(uxj.h), f2s(uxj.l)};
       const ff2 thinv2{f2s(thinv.h), f2s(thinv.l)};
       float b1 = -1.0f, b2 = -1.0f;
@@ -361,10 +367,10 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       for (int qq = tid; qq < jd * (jd + 1); qq += MB) {
         const int a = qq / (jd + 1), b = qq % (jd + 1);
         if (b < jd && b > a) continue;
-        const double *xa = P.X + (int64_t)cnd[dr[a]] * p;
+        const double *xa = L.X + (int64_t)cnd[dr[a]] * p;
         double val;
-        if (b < jd) val = (a == b) ? P.onepg : corr64(xa, P.X + (int64_t)cnd[dr[b]] * p, p, P.theta_inv, etab);
-        else val = corr64(xa, xl, p, P.theta_inv, etab);
+        if (b < jd) val = (a == b) ? L.onepg : corr64(xa, L.X + (int64_t)cnd[dr[b]] * p, p, L.theta_inv, etab);
+        else val = corr64(xa, xl, p, L.theta_inv, etab);
         A[a * lda + b] = val;
       }
       __syncthreads();
@@ -378,15 +384,15 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       for (int item = warp; item < nl; item += MB / 32) {
         const int c = all ? item : rlist[item];
         if (used[c]) continue;
-        const double *xc = P.X + (int64_t)cnd[c] * p;
+        const double *xc = L.X + (int64_t)cnd[c] * p;
         double tv[kMaxN / 32];
 #pragma unroll
         for (int r = 0; r < kMaxN / 32; r++) {
           const int i = 32 * r + lane;
-          tv[r] = (i < jd) ? corr64(P.X + (int64_t)cnd[dr[i]] * p, xc, p, P.theta_inv, etab) : 0.0;
+          tv[r] = (i < jd) ? corr64(L.X + (int64_t)cnd[dr[i]] * p, xc, p, L.theta_inv, etab) : 0.0;
         }
-        double vsum = P.onepg;
-        double cov = corr64(xl, xc, p, P.theta_inv, etab);
+        double vsum = L.onepg;
+        double cov = corr64(xl, xc, p, L.theta_inv, etab);
         for (int m = 0; m < jd; m++) {
           double own = 0.0;
 #pragma unroll
@@ -435,11 +441,11 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       for (int qq = tid; qq < n * (n + 2); qq += MB) {
         const int a = qq / (n + 2), b = qq % (n + 2);
         if (b < n && b > a) continue;  // only the lower triangle is read
-        const double *xa = P.X + (int64_t)cnd[dr[a]] * p;
+        const double *xa = L.X + (int64_t)cnd[dr[a]] * p;
         double val;
-        if (b < n) val = (a == b) ? P.onepg : corr64(xa, P.X + (int64_t)cnd[dr[b]] * p, p, P.theta_inv, etab);
-        else if (b == n) val = corr64(xa, xl, p, P.theta_inv, etab);
-        else val = P.Z[cnd[dr[a]]];
+        if (b < n) val = (a == b) ? L.onepg : corr64(xa, L.X + (int64_t)cnd[dr[b]] * p, p, L.theta_inv, etab);
+        else if (b == n) val = corr64(xa, xl, p, L.theta_inv, etab);
+        else val = L.Z[cnd[dr[a]]];
         A[a * lda + b] = val;
       }
       __syncthreads();
@@ -453,7 +459,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
         P.s2[loc] = NAN;
         if (P.var) P.var[loc] = NAN;
       } else {
-        double mu = 0.0, psi = 0.0, vx = P.onepg;
+        double mu = 0.0, psi = 0.0, vx = L.onepg;
         for (int i = 0; i < n; i++) {
           const double ux = A[i * lda + n], yt = A[i * lda + n + 1];
           mu = fma(ux, yt, mu);
@@ -467,8 +473,8 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
         if (P.status) P.status[loc] = 0;
       }
     }
-    if (P.idx) {
-      for (int i = tid; i < n; i += MB) P.idx[loc * n + i] = sh_fail ? -1 : cnd[dr[i]];
+    if (L.idx) {
+      for (int i = tid; i < n; i += MB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
     }
   }
 }
@@ -521,6 +527,8 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = mix_mpad(a.M); P.Qpad = P.Mpad / 2; P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
+  P.nmax = a.n; P.pmax = a.p;
+  P.B = BatchView{nullptr, nullptr, nullptr, 0};
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.rescores = reinterpret_cast<int *>(w + 256);
@@ -538,5 +546,45 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   g_launches.fetch_add(1);
   return cuda_status(cudaGetLastError());
 }
+
+size_t select_mixed_batch_workspace_bytes(const BatchLaunch &b, int G) {
+  return mix_layout(G, b.pmax, b.nmax, b.Mmax).total;
+}
+
+int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G,
+                              cudaStream_t stream) {
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st) return st;
+  st = exp_table_upload();  // this translation unit's copy of the exp constants
+  if (st) return st;
+  const MixLayout L = mix_layout(G, b.pmax, b.nmax, b.Mmax);
+  if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
+  char *w = static_cast<char *>(ws);
+  MixParams P;
+  P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
+  P.M = b.Mmax; P.Mpad = mix_mpad(b.Mmax); P.Qpad = P.Mpad / 2; P.n0 = 0; P.n = b.nmax;
+  P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
+  P.nmax = b.nmax; P.pmax = b.pmax;
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx};
+  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
+  P.queue = reinterpret_cast<int *>(w);
+  P.rescores = reinterpret_cast<int *>(w + 256);
+  P.U = reinterpret_cast<float4 *>(w + 512);
+  P.Xr = reinterpret_cast<float4 *>(w + 512 + L.u);
+  P.A = reinterpret_cast<double *>(w + 512 + L.u + L.xr);
+  const size_t smem = mix_smem_bytes(P.Mpad, b.nmax);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_mixed_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(w, 0, 512, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  select_mixed_kernel<<<G, MB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  return cuda_status(cudaGetLastError());
+}
+
+int select_mixed_prepare() { return exp_table_upload(); }
 
 }  // namespace lagp

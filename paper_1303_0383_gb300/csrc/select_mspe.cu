@@ -20,6 +20,7 @@
 // ||r||^2 and (ytil . r)^2, all updated as rows are appended.
 #include <math.h>
 
+#include "batch.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -35,7 +36,9 @@ struct MspeParams {
   int64_t T;
   const int32_t *cand;
   int M, Mpad, n0, n;
-  double theta, theta_inv, onepg;
+  int nmax, pmax;  // slot dimensions (the largest n and p of the launch)
+  double theta, theta_inv, g, onepg;
+  BatchView B;     // per-location tables (B.designs == nullptr: uniform launch)
   double *mean, *s2, *var;
   int32_t *idx;
   int8_t *status;
@@ -52,21 +55,21 @@ __device__ __forceinline__ bool j_better(double a, int ra, double b, int rb) {
 
 __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
   extern __shared__ __align__(16) double sm[];
-  const int Mpad = P.Mpad, n = P.n, p = P.p, M = P.M;
+  const int Mpad = P.Mpad, nn = P.nmax;  // nn: row stride of the n x n slot matrices
   double *v = sm;               // Mpad: v_j(c)
   double *cov = v + Mpad;       // Mpad: cov_j(x, c)
-  double *srow = cov + Mpad;    // n: u_s
-  double *sdrow = srow + n;     // n: ud_s
-  double *qrow = sdrow + n;     // n: row j of Q
-  double *rrow = qrow + n;      // n: row j of R
-  double *ux = rrow + n;        // n: L^{-1} k(x)
-  double *udx = ux + n;         // n: L^{-1} kd(x)
-  double *yt = udx + n;         // n: L^{-1} Y
-  double *r = yt + n;           // n: Q ytil
-  double *t1 = r + n;           // n: Kd Li[j]^T
-  double *t2 = t1 + n;          // n: Kdd Li[j]^T
-  int *dr = reinterpret_cast<int *>(t2 + n);  // n: ranks of the design
-  unsigned char *used = reinterpret_cast<unsigned char *>(dr + n);  // Mpad
+  double *srow = cov + Mpad;    // nn: u_s
+  double *sdrow = srow + nn;    // nn: ud_s
+  double *qrow = sdrow + nn;    // nn: row j of Q
+  double *rrow = qrow + nn;     // nn: row j of R
+  double *ux = rrow + nn;       // nn: L^{-1} k(x)
+  double *udx = ux + nn;        // nn: L^{-1} kd(x)
+  double *yt = udx + nn;        // nn: L^{-1} Y
+  double *r = yt + nn;          // nn: Q ytil
+  double *t1 = r + nn;          // nn: Kd Li[j]^T
+  double *t2 = t1 + nn;         // nn: Kdd Li[j]^T
+  int *dr = reinterpret_cast<int *>(t2 + nn);  // nn: ranks of the design
+  unsigned char *used = reinterpret_cast<unsigned char *>(dr + nn);  // Mpad
   __shared__ double etab[64];
   __shared__ double xs[kMaxP], xl[kMaxP];
   __shared__ double red_s[TB / 32];
@@ -77,33 +80,36 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
   __shared__ double sh_psi, sh_vx, sh_trR, sh_nQ2, sh_yRy;
   if (threadIdx.x < 64) etab[threadIdx.x] = c_exp.tab[threadIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double *U = P.U + (size_t)blockIdx.x * n * Mpad;
-  double *Ud = P.Ud + (size_t)blockIdx.x * n * Mpad;
-  double *Xc = P.Xc + (size_t)blockIdx.x * p * Mpad;
+  double *U = P.U + (size_t)blockIdx.x * nn * Mpad;
+  double *Ud = P.Ud + (size_t)blockIdx.x * nn * Mpad;
+  double *Xc = P.Xc + (size_t)blockIdx.x * P.pmax * Mpad;
   double *cs = P.cs + (size_t)blockIdx.x * 4 * Mpad;
   double *kdz = cs, *pd = cs + Mpad, *qc = cs + 2 * Mpad, *mc = cs + 3 * Mpad;
-  double *Li = P.Li + (size_t)blockIdx.x * n * n;
-  double *Kd = P.Kd + (size_t)blockIdx.x * n * n;
-  double *Kdd = P.Kdd + (size_t)blockIdx.x * n * n;
-  double *Q = P.Q + (size_t)blockIdx.x * n * n;
-  const double th = P.theta, th2 = th * th, th3 = th2 * th, th4 = th2 * th2;
+  double *Li = P.Li + (size_t)blockIdx.x * nn * nn;
+  double *Kd = P.Kd + (size_t)blockIdx.x * nn * nn;
+  double *Kdd = P.Kdd + (size_t)blockIdx.x * nn * nn;
+  double *Q = P.Q + (size_t)blockIdx.x * nn * nn;
 
   for (;;) {
     __syncthreads();
     if (tid == 0) sh_loc = atomicAdd(P.queue, 1);
     __syncthreads();
-    const int64_t loc = sh_loc;
-    if (loc >= P.T) break;
-    const int32_t *cnd = P.cand + loc * M;
-    if (tid < p) xl[tid] = P.XX[loc * p + tid];
+    if (sh_loc >= P.T) break;
+    const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, P.M, P.n0, P.theta,
+                                    P.g, P.cand, P.idx);
+    const int64_t loc = L.loc;
+    const int n = L.n, p = L.p, M = L.M;
+    const int32_t *cnd = L.cand;
+    const double th = L.theta, th2 = th * th, th3 = th2 * th, th4 = th2 * th2;
+    if (tid < p) xl[tid] = L.x[tid];
     if (tid == 0) {
       sh_fail = 0;
-      sh_psi = 0.0; sh_vx = P.onepg; sh_trR = 0.0; sh_nQ2 = 0.0; sh_yRy = 0.0;
+      sh_psi = 0.0; sh_vx = L.onepg; sh_trR = 0.0; sh_nQ2 = 0.0; sh_yRy = 0.0;
     }
     __syncthreads();
-    const int limit = (P.n0 == n) ? n : M;
+    const int limit = (L.n0 == n) ? n : M;
     for (int c = tid; c < limit; c += TB) {
-      const double *xc = P.X + (int64_t)cnd[c] * p;
+      const double *xc = L.X + (int64_t)cnd[c] * p;
       double acc = 0.0;
       for (int k = 0; k < p; k++) {
         const double xk = xc[k];
@@ -111,15 +117,15 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
         const double t = xl[k] - xk;
         acc = fma(t, t, acc);
       }
-      v[c] = P.onepg;
-      cov[c] = exp_nonpos(-acc * P.theta_inv, etab);
+      v[c] = L.onepg;
+      cov[c] = exp_nonpos(-acc * L.theta_inv, etab);
       kdz[c] = 0.0; pd[c] = 0.0; qc[c] = 0.0; mc[c] = 0.0;
       used[c] = 0;
     }
     __syncthreads();
 
     for (int j = 0; j < n; j++) {
-      const int s = (j < P.n0) ? j : sh_best;
+      const int s = (j < L.n0) ? j : sh_best;
       if (s < 0) {
         if (tid == 0) sh_fail = 1;
         __syncthreads();
@@ -155,10 +161,10 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
           const double t = xl[k] - xs[k];
           acc = fma(t, t, acc);
         }
-        const double kxs = exp_nonpos(-acc * P.theta_inv, etab);
+        const double kxs = exp_nonpos(-acc * L.theta_inv, etab);
         const double kdxs = kxs * acc / th2;
         const double uxj = cov[s] / sq;
-        const double ytj = (P.Z[cnd[s]] - sh_dot[0]) / sq;
+        const double ytj = (L.Z[cnd[s]] - sh_dot[0]) / sq;
         ux[j] = uxj;
         udx[j] = (kdxs - sh_dot[1]) * inv;
         yt[j] = ytj;
@@ -179,24 +185,24 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
           li = inv;
         } else {
           double acc = 0.0;
-          for (int m = i; m < j; m++) acc = fma(srow[m], Li[(size_t)m * n + i], acc);
+          for (int m = i; m < j; m++) acc = fma(srow[m], Li[(size_t)m * nn + i], acc);
           li = -acc * inv;
         }
-        Li[(size_t)j * n + i] = li;
+        Li[(size_t)j * nn + i] = li;
         double kd = 0.0, kdd = 0.0;
         if (i < j) {
-          const double *xi = P.X + (int64_t)cnd[dr[i]] * p;
+          const double *xi = L.X + (int64_t)cnd[dr[i]] * p;
           double acc = 0.0;
           for (int k = 0; k < p; k++) {
             const double t = xs[k] - xi[k];
             acc = fma(t, t, acc);
           }
-          const double kk = exp_nonpos(-acc * P.theta_inv, etab);
+          const double kk = exp_nonpos(-acc * L.theta_inv, etab);
           kd = kk * acc / th2;
           kdd = kk * (acc * acc / th4 - 2.0 * acc / th3);
         }
-        Kd[(size_t)j * n + i] = kd;
-        Kdd[(size_t)j * n + i] = kdd;
+        Kd[(size_t)j * nn + i] = kd;
+        Kdd[(size_t)j * nn + i] = kdd;
       }
       __syncthreads();
       // t1 = Kd Li[j]^T, t2 = Kdd Li[j]^T over rows a <= j (symmetric: entry (a,c) at row max)
@@ -204,9 +210,9 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
         double s1 = 0.0, s2 = 0.0;
         for (int c = 0; c <= j; c++) {
           const int hi = a > c ? a : c, lo = a > c ? c : a;
-          const double lj = Li[(size_t)j * n + c];
-          s1 = fma(Kd[(size_t)hi * n + lo], lj, s1);
-          s2 = fma(Kdd[(size_t)hi * n + lo], lj, s2);
+          const double lj = Li[(size_t)j * nn + c];
+          s1 = fma(Kd[(size_t)hi * nn + lo], lj, s1);
+          s2 = fma(Kdd[(size_t)hi * nn + lo], lj, s2);
         }
         t1[a] = s1;
         t2[a] = s2;
@@ -216,11 +222,11 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
       for (int b = tid; b <= j; b += TB) {
         double s1 = 0.0, s2 = 0.0;
         for (int a = 0; a <= b; a++) {
-          const double l = Li[(size_t)b * n + a];
+          const double l = Li[(size_t)b * nn + a];
           s1 = fma(l, t1[a], s1);
           s2 = fma(l, t2[a], s2);
         }
-        Q[(size_t)j * n + b] = s1;
+        Q[(size_t)j * nn + b] = s1;
         qrow[b] = s1;
         rrow[b] = s2;
       }
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
       const double uxj = sh_d[1], rj = sh_d[3], F = sh_d[4], dmux = sh_d[5], wKdw = sh_d[6];
       const double psi = sh_psi, vx = sh_vx, qjj = qrow[j];
       const int jn = j + 1;  // design size after this step
-      const bool want = (jn >= P.n0) && (jn >= 3);
+      const bool want = (jn >= L.n0) && (jn >= 3);
       const double dj = (double)(jn - 2);
       double bs = INFINITY;
       int br = 0x7fffffff;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
           const double t = xs[k] - Xc[k * Mpad + c];
           acc = fma(t, t, acc);
         }
-        const double ksc = exp_nonpos(-acc * P.theta_inv, etab);
+        const double ksc = exp_nonpos(-acc * L.theta_inv, etab);
         const double kdsc = ksc * acc / th2;
         double d1 = ksc, d2 = kdsc, d3 = 0.0;
         const double *Uc = U + c, *Udc = Ud + c;
@@ -365,8 +371,8 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
         if (P.status) P.status[loc] = 0;
       }
     }
-    if (P.idx)
-      for (int i = tid; i < n; i += TB) P.idx[loc * n + i] = sh_fail ? -1 : cnd[dr[i]];
+    if (L.idx)
+      for (int i = tid; i < n; i += TB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
   }
 }
 
@@ -416,7 +422,9 @@ int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStrea
   MspeParams P;
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = (int)align_up((size_t)a.M, 32); P.n0 = a.n0; P.n = a.n;
-  P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.onepg = 1.0 + a.g;
+  P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
+  P.nmax = a.n; P.pmax = a.p;
+  P.B = BatchView{nullptr, nullptr, nullptr, 0};
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   size_t off = 256;
@@ -439,5 +447,50 @@ int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStrea
   g_launches.fetch_add(1);
   return cuda_status(cudaGetLastError());
 }
+
+size_t select_mspe_batch_workspace_bytes(const BatchLaunch &b, int G) {
+  return mspe_layout(G, b.pmax, b.nmax, b.Mmax).total;
+}
+
+int select_mspe_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G,
+                             cudaStream_t stream) {
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st) return st;
+  st = exp_table_upload();  // this translation unit's copy of the exp constants
+  if (st) return st;
+  const MspeLayout L = mspe_layout(G, b.pmax, b.nmax, b.Mmax);
+  if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
+  char *w = static_cast<char *>(ws);
+  MspeParams P;
+  P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
+  P.M = b.Mmax; P.Mpad = (int)align_up((size_t)b.Mmax, 32); P.n0 = 0; P.n = b.nmax;
+  P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
+  P.nmax = b.nmax; P.pmax = b.pmax;
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx};
+  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
+  P.queue = reinterpret_cast<int *>(w);
+  size_t off = 256;
+  P.U = reinterpret_cast<double *>(w + off); off += L.u;
+  P.Ud = reinterpret_cast<double *>(w + off); off += L.ud;
+  P.Xc = reinterpret_cast<double *>(w + off); off += L.xc;
+  P.cs = reinterpret_cast<double *>(w + off); off += L.cs;
+  P.Li = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.Kd = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.Kdd = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.Q = reinterpret_cast<double *>(w + off); off += L.nn;
+  const size_t smem = mspe_smem_bytes(P.Mpad, b.nmax);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_mspe_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  select_mspe_kernel<<<G, TB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  return cuda_status(cudaGetLastError());
+}
+
+int select_mspe_prepare() { return exp_table_upload(); }
 
 }  // namespace lagp

@@ -69,6 +69,10 @@ def load(path: str | None = None):
     L.lagp_predict_dev.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32, i32,
                                    P, P, P, P, P, P, sz, P]
     L.lagp_exp_dev.argtypes = [P, P, i64, P]
+    L.lagp_predict_batch_workspace_bytes.argtypes = [P, i32, i64, P, P, P, i32, i32]
+    L.lagp_predict_batch_workspace_bytes.restype = sz
+    L.lagp_predict_batch_dev.argtypes = [P, i32, P, i32, i64, P, P, P, i32, i32, P, P, P, P, P,
+                                         ctypes.c_uint32, P, sz, P]
     L.lagp_select_dev_noalloc.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
                                           i32, i32, P, P, P, P, P, P]
     _lib = L
@@ -157,6 +161,49 @@ def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2
 def lagp_exp_dev(x, y, stream=None) -> None:
     """The library's FP64 exponential elementwise (device tensors, float64)."""
     _chk(load().lagp_exp_dev(_dp(x), _dp(y), x.numel(), _stream(stream)), "lagp_exp_dev")
+
+
+LAGP_BATCH_TUNE, LAGP_BATCH_GRAPH = 1, 2
+
+
+class DesignDesc(ctypes.Structure):
+    """lagp_design_desc: one resident design of a batch (device X, Z)."""
+    _fields_ = [("X", ctypes.c_void_p), ("Z", ctypes.c_void_p), ("N", ctypes.c_int64),
+                ("p", ctypes.c_int32), ("n0", ctypes.c_int32), ("theta", ctypes.c_double),
+                ("g", ctypes.c_double)]
+
+
+def _descs(designs):
+    """designs: sequence of dicts with X, Z (CUDA tensors), n0, theta, g."""
+    arr = (DesignDesc * len(designs))()
+    for i, d in enumerate(designs):
+        X, Z = d["X"], d["Z"]
+        if not (X.is_cuda and Z.is_cuda and X.is_contiguous() and Z.is_contiguous()):
+            raise ValueError("design tensors must be contiguous CUDA tensors")
+        arr[i] = DesignDesc(X.data_ptr(), Z.data_ptr(), X.shape[0], X.shape[1], int(d["n0"]),
+                            float(d["theta"]), float(d["g"]))
+    return arr
+
+
+def lagp_predict_batch_workspace_bytes(designs, design_of, n, ncand, method="alc",
+                                       precision="fp64") -> int:
+    a = _descs(designs)
+    do, nn, nc = (np.ascontiguousarray(x, dtype=np.int32) for x in (design_of, n, ncand))
+    return int(load().lagp_predict_batch_workspace_bytes(a, len(designs), do.shape[0], _hp(do),
+                                                         _hp(nn), _hp(nc), _m(method),
+                                                         _pr(precision)))
+
+
+def lagp_predict_batch_dev(designs, XX, design_of, n, ncand, method, precision, mean, s2,
+                           var=None, idx=None, status=None, flags=0, ws=None, stream=None) -> None:
+    """Batched path: XX is a (T, ldxx) CUDA tensor, design_of/n/ncand host int arrays."""
+    a = _descs(designs)
+    do, nn, nc = (np.ascontiguousarray(x, dtype=np.int32) for x in (design_of, n, ncand))
+    T, ldxx = XX.shape
+    _chk(load().lagp_predict_batch_dev(a, len(designs), _dp(XX), ldxx, T, _hp(do), _hp(nn),
+                                       _hp(nc), _m(method), _pr(precision), _dp(mean), _dp(s2),
+                                       _dp(var), _dp(idx), _dp(status), flags, _dp(ws),
+                                       ws.numel(), _stream(stream)), "lagp_predict_batch_dev")
 
 
 def lagp_select_dev_noalloc(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2,

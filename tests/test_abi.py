@@ -74,3 +74,23 @@ def test_null_design_and_bad_knn_args():
         lagp.LAGP_ERR_INVALID_ARG            # ncand > N
     assert L.lagp_knn_dev(P(1), 10, 2, P(1), 3, 5, P(1), P(8), 1 << 20, None) == \
         lagp.LAGP_ERR_INVALID_ARG            # misaligned workspace
+
+
+def test_batch_arguments_are_checked_on_the_host():
+    import ctypes as C
+    L = lagp.load()
+    designs = (lagp.DesignDesc * 2)(lagp.DesignDesc(1, 1, 1000, 2, 4, 0.5, 1e-6),
+                                    lagp.DesignDesc(1, 1, 500, 8, 6, 1.0, 1e-4))
+    def call(do, n, m, method=0, precision=0, ldxx=8):
+        do, n, m = (np.ascontiguousarray(x, dtype=np.int32) for x in (do, n, m))
+        P = C.c_void_p
+        return L.lagp_predict_batch_dev(designs, 2, P(1), ldxx, len(n), lagp._hp(do), lagp._hp(n),
+                                        lagp._hp(m), method, precision, P(1), P(1), None, None,
+                                        None, 0, P(256), 1 << 30, None)
+    assert call([0, 1], [10, 5], [50, 40]) == lagp.LAGP_ERR_INVALID_ARG      # n < n0 of design 1
+    assert call([0, 2], [10, 10], [50, 40]) == lagp.LAGP_ERR_INVALID_ARG     # design index
+    assert call([0, 1], [10, 10], [9, 40]) == lagp.LAGP_ERR_INVALID_ARG      # ncand < n
+    assert call([0, 1], [10, 10], [50, 501]) == lagp.LAGP_ERR_INVALID_ARG    # ncand > N
+    assert call([0, 1], [10, 300], [50, 400]) == lagp.LAGP_ERR_INVALID_ARG   # n > 256
+    assert call([0, 1], [10, 10], [50, 40], ldxx=4) == lagp.LAGP_ERR_INVALID_ARG  # ldxx < p
+    assert call([0, 1], [10, 10], [50, 40], method=1, precision=1) == lagp.LAGP_ERR_UNSUPPORTED
