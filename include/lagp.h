@@ -185,6 +185,37 @@ int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t ndesigns, co
                            double *s2, double *var, int32_t *idx, int8_t *status, uint32_t flags,
                            void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------------ serving loop */
+/* A continuous-batching server over resident designs (the paper's global emulation of
+ * Sec. 4, served request by request).  A request is a block of L locations against one
+ * design with its n and candidate count.  A scheduler thread coalesces queued requests
+ * into batches (lagp_predict_batch_dev) and runs each on one of a few in-flight slots
+ * (own stream, device buffers and pinned staging), so requests arriving while other
+ * batches run are admitted as soon as a slot frees and their work overlaps on the device.
+ * Admission is bounded by device memory: slots = min(max_slots, memory_budget / bytes of
+ * one slot sized for max_batch locations with nmax and ncand_max).  Results of a request
+ * do not depend on what else was batched with it (bitwise).
+ * lagp_server_create copies the design descriptors (the designs' device X, Z must stay
+ * valid until destroy) and allocates every slot up front (LAGP_ERR_OOM if not even one
+ * fits the budget).  submit copies XX (host, L x p) and returns at once; wait blocks up
+ * to timeout_ms (negative: no limit) for a request; results copies a finished request's
+ * outputs to host buffers (mean, s2, var: L; idx: L x n; status: L; any may be NULL),
+ * gives its latency from submit to completion in ms, and forgets the request. */
+typedef struct lagp_server lagp_server;
+int lagp_server_create(const lagp_design_desc *designs, int32_t ndesigns, int32_t method,
+                       int32_t precision, int32_t nmax, int32_t ncand_max, int64_t max_batch,
+                       size_t memory_budget, int32_t max_slots, lagp_server **out);
+int lagp_server_submit(lagp_server *s, int32_t design, const double *XX, int64_t L, int32_t n,
+                       int32_t ncand, uint64_t *request_id);
+int lagp_server_wait(lagp_server *s, uint64_t request_id, int32_t timeout_ms, int32_t *done);
+int lagp_server_results(lagp_server *s, uint64_t request_id, double *mean, double *s2,
+                        double *var, int32_t *idx, int8_t *status, double *latency_ms);
+/* Batches and locations completed, slots, the most batches seen in flight at once; the
+ * return value is the last error a batch met (LAGP_OK if none). */
+int lagp_server_stats(lagp_server *s, int64_t *batches, int64_t *locations, int32_t *slots,
+                      int32_t *max_inflight);
+int lagp_server_destroy(lagp_server *s);
+
 /* ------------------------------------------------------------------ no-allocation variant */
 /* Kernels (b)+(c) as lagp_select_dev, for callers that cannot allocate device memory: a
  * plugin running inside a host application that owns every device allocation and forbids

@@ -110,3 +110,46 @@ def random_case(seed: int, N: int, p: int, T: int, n0: int, n: int, ncand: int,
     Z = np.sin(X @ a) + 0.5 * np.cos(3.0 * X[:, 0])
     return Workload("random seed=%d N=%d p=%d T=%d" % (seed, N, p, T), X, Z, XX,
                     n0=n0, n=n, ncand=ncand, d=d, g=g)
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    """Uneven local problems across several resident designs (one persistent launch)."""
+    name: str
+    designs: list          # list of Workload (X, Z, n0, d, g used; XX empty)
+    design_of: np.ndarray  # T int32
+    n: np.ndarray          # T int32
+    ncand: np.ndarray      # T int32
+    XX: np.ndarray         # T x 8, row t holds its design's p coordinates first
+
+    @property
+    def T(self) -> int:
+        return int(self.n.shape[0])
+
+
+def batched_uneven(T: int = 20000) -> BatchWorkload:
+    """Three resident designs: the paper-scale 2-d design (N=40000, d=0.5, g=1e-6, n0=6), a
+    4-d design N=200000 uniform on [0,1]^4 with z = prod_j sin(3 x_j) (d=0.2, g=1e-6, n0=6),
+    and the 8-d design (N=100000, d=1, g=1e-4, n0=8).  T locations, a third per design at
+    random, each uniform on its design's domain; n uniform on {30..200} and the candidate
+    count uniform on {500..4000}, independently."""
+    d2 = paper_2d()
+    d8 = smooth_8d(T=1)
+    rng = np.random.default_rng(SEED_BASE + 4)
+    X4 = rng.uniform(0.0, 1.0, size=(200000, 4))
+    d4 = Workload("4-d N=200000", X4, _surface_4d(X4), np.zeros((0, 4)), n0=6, n=30, ncand=500,
+                  d=0.2, g=1e-6)
+    designs = [Workload(d2.name, d2.X, d2.Z, np.zeros((0, 2)), d2.n0, 30, 500, d2.d, d2.g), d4,
+               Workload(d8.name, d8.X, d8.Z, np.zeros((0, 8)), d8.n0, 30, 500, d8.d, d8.g)]
+    design_of = rng.integers(0, 3, size=T).astype(np.int32)
+    n = rng.integers(30, 201, size=T).astype(np.int32)
+    ncand = rng.integers(500, 4001, size=T).astype(np.int32)
+    XX = np.zeros((T, 8))
+    lo = {0: -2.0, 1: 0.0, 2: 0.0}
+    hi = {0: 2.0, 1: 1.0, 2: 1.0}
+    for t in range(T):
+        d = int(design_of[t])
+        p = designs[d].p
+        XX[t, :p] = rng.uniform(lo[d], hi[d], size=p)
+    return BatchWorkload("batched-uneven T=%d over 2-d/4-d/8-d designs, n~U{30..200}, "
+                         "ncand~U{500..4000}" % T, designs, design_of, n, ncand, XX)

@@ -69,6 +69,13 @@ def load(path: str | None = None):
     L.lagp_predict_dev.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32, i32,
                                    P, P, P, P, P, P, sz, P]
     L.lagp_exp_dev.argtypes = [P, P, i64, P]
+    L.lagp_server_create.argtypes = [P, i32, i32, i32, i32, i32, i64, sz, i32, ctypes.POINTER(P)]
+    L.lagp_server_submit.argtypes = [P, i32, P, i64, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    L.lagp_server_wait.argtypes = [P, ctypes.c_uint64, i32, ctypes.POINTER(i32)]
+    L.lagp_server_results.argtypes = [P, ctypes.c_uint64, P, P, P, P, P, ctypes.POINTER(f64)]
+    L.lagp_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.lagp_server_destroy.argtypes = [P]
     L.lagp_predict_batch_workspace_bytes.argtypes = [P, i32, i64, P, P, P, i32, i32]
     L.lagp_predict_batch_workspace_bytes.restype = sz
     L.lagp_predict_batch_dev.argtypes = [P, i32, P, i32, i64, P, P, P, i32, i32, P, P, P, P, P,
@@ -204,6 +211,64 @@ def lagp_predict_batch_dev(designs, XX, design_of, n, ncand, method, precision, 
                                        _hp(nc), _m(method), _pr(precision), _dp(mean), _dp(s2),
                                        _dp(var), _dp(idx), _dp(status), flags, _dp(ws),
                                        ws.numel(), _stream(stream)), "lagp_predict_batch_dev")
+
+
+class Server:
+    """lagp_server_*: continuous-batching serving loop over resident designs."""
+
+    def __init__(self, designs, method="alc", precision="mixed", nmax=128, ncand_max=2048,
+                 max_batch=16384, memory_budget=8 << 30, max_slots=4):
+        self._designs = designs          # keeps the device tensors alive
+        self._descs = _descs(designs)
+        self._p = [int(d["X"].shape[1]) for d in designs]
+        h = ctypes.c_void_p()
+        _chk(load().lagp_server_create(self._descs, len(designs), _m(method), _pr(precision), nmax,
+                                       ncand_max, max_batch, memory_budget, max_slots,
+                                       ctypes.byref(h)), "lagp_server_create")
+        self._h = h
+        self._n = {}
+
+    def submit(self, design, XX, n, ncand) -> int:
+        XX = np.ascontiguousarray(XX, dtype=np.float64)
+        rid = ctypes.c_uint64()
+        _chk(load().lagp_server_submit(self._h, design, _hp(XX), XX.shape[0], n, ncand,
+                                       ctypes.byref(rid)), "lagp_server_submit")
+        self._n[rid.value] = (XX.shape[0], n)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=-1) -> bool:
+        done = ctypes.c_int32()
+        _chk(load().lagp_server_wait(self._h, rid, timeout_ms, ctypes.byref(done)), "lagp_server_wait")
+        return bool(done.value)
+
+    def results(self, rid):
+        L, n = self._n.pop(rid)
+        out = dict(mean=np.empty(L), s2=np.empty(L), var=np.empty(L),
+                   idx=np.empty((L, n), np.int32), status=np.empty(L, np.int8))
+        lat = ctypes.c_double()
+        _chk(load().lagp_server_results(self._h, rid, _hp(out["mean"]), _hp(out["s2"]),
+                                        _hp(out["var"]), _hp(out["idx"]), _hp(out["status"]),
+                                        ctypes.byref(lat)), "lagp_server_results")
+        out["latency_ms"] = lat.value
+        return out
+
+    def stats(self):
+        b, l, s, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        code = load().lagp_server_stats(self._h, ctypes.byref(b), ctypes.byref(l), ctypes.byref(s),
+                                        ctypes.byref(m))
+        return dict(batches=b.value, locations=l.value, slots=s.value, max_inflight=m.value,
+                    last_error=code)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _chk(load().lagp_server_destroy(self._h), "lagp_server_destroy")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lagp_select_dev_noalloc(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2,

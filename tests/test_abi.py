@@ -94,3 +94,20 @@ def test_batch_arguments_are_checked_on_the_host():
     assert call([0, 1], [10, 300], [50, 400]) == lagp.LAGP_ERR_INVALID_ARG   # n > 256
     assert call([0, 1], [10, 10], [50, 40], ldxx=4) == lagp.LAGP_ERR_INVALID_ARG  # ldxx < p
     assert call([0, 1], [10, 10], [50, 40], method=1, precision=1) == lagp.LAGP_ERR_UNSUPPORTED
+
+
+def test_server_arguments_are_checked_on_the_host():
+    import ctypes as C
+    L = lagp.load()
+    designs = (lagp.DesignDesc * 1)(lagp.DesignDesc(1, 1, 1000, 2, 4, 0.5, 1e-6))
+    out = C.c_void_p()
+    bad = [dict(nd=0), dict(nmax=2), dict(nmax=300), dict(ncand=10, nmax=20), dict(ncand=9000),
+           dict(max_batch=0), dict(max_slots=0)]
+    for b in bad:
+        a = dict(nd=1, method=0, precision=1, nmax=64, ncand=400, max_batch=1024, budget=1 << 30,
+                 max_slots=2)
+        a.update(b)
+        assert L.lagp_server_create(designs, a["nd"], a["method"], a["precision"], a["nmax"],
+                                    a["ncand"], a["max_batch"], a["budget"], a["max_slots"],
+                                    C.byref(out)) == lagp.LAGP_ERR_INVALID_ARG, b
+    assert L.lagp_server_destroy(None) == lagp.LAGP_ERR_INVALID_ARG
