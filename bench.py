@@ -450,6 +450,81 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Workload 5: Poisson arrivals of requests (1..4096 locations, log-uniform) against
+    the three resident designs with n in {50, 100}; p50/p99 latency and throughput per
+    arrival rate, for the server in each precision."""
+    import threading
+    import torch
+    from paper_1303_0383_gb300 import inputs, lagp
+    lagp.load()
+    B = inputs.batched_uneven(1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    descs = [dict(X=torch.as_tensor(w.X, device=dev), Z=torch.as_tensor(w.Z, device=dev),
+                  n0=w.n0, theta=w.d, g=w.g) for w in B.designs]
+    ncand = [1000, 2000, 2000]
+    lo, hi = [-2.0, 0.0, 0.0], [2.0, 1.0, 1.0]
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    results = {}
+    for prec in precs:
+        srv = lagp.Server(descs, "alc", prec, nmax=100, ncand_max=2000, max_batch=16384,
+                          memory_budget=24 << 30, max_slots=3)
+        # warm-up: one request per design and n
+        for d in range(3):
+            for n in (50, 100):
+                rid = srv.submit(d, np.random.default_rng(d).uniform(lo[d], hi[d], (64, B.designs[d].p)),
+                                 n, ncand[d])
+                srv.wait(rid, -1)
+                srv.results(rid)
+        per_rate = {}
+        for lam in rates:
+            rng = np.random.default_rng(int(lam))
+            sent = []
+            t_end = args.serve_seconds
+            start = time.perf_counter()
+            t_next = 0.0
+            while t_next < t_end:
+                L = int(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))))
+                d = int(rng.integers(0, 3))
+                n = int(rng.choice([50, 100]))
+                x = rng.uniform(lo[d], hi[d], size=(L, B.designs[d].p))
+                now = time.perf_counter() - start
+                if t_next > now:
+                    time.sleep(t_next - now)
+                sent.append((srv.submit(d, x, n, ncand[d]), L))
+                t_next += rng.exponential(L / lam)   # arrivals carry L locations at rate lam
+            lat, locs = [], 0
+            for rid, L in sent:
+                srv.wait(rid, -1)
+                r = srv.results(rid)
+                assert (r["status"] == 0).all()
+                lat.append(r["latency_ms"])
+                locs += L
+            wall = time.perf_counter() - start
+            lat = np.array(lat)
+            per_rate[str(int(lam))] = {
+                "requests": len(sent), "locations": locs,
+                "throughput_locations_per_s": locs / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean())}
+        st = srv.stats()
+        srv.close()
+        results[prec] = {"rates": per_rate, "slots": st["slots"], "max_inflight": st["max_inflight"],
+                         "batches": st["batches"]}
+    top = str(int(max(rates)))
+    head = "mixed" if "mixed" in results else precs[0]
+    print(json.dumps({
+        "metric": "serving p99 ms (Poisson arrivals, 1..4096 locations per request)",
+        "value": results[head]["rates"][top]["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": "serving over the 2-d/4-d/8-d designs, n in {50,100}, candidates "
+                               "1000/2000/2000, %g s per rate" % args.serve_seconds,
+                   "rates_locations_per_s": rates, "headline_rate": top, "precision": head},
+        "results": results}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,7 +538,9 @@ def main():
                     help="use only the first K locations (small case for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-API timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--workload", default="paper-2d", choices=["paper-2d", "batched"])
+    ap.add_argument("--workload", default="paper-2d", choices=["paper-2d", "batched", "serving"])
+    ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--batch-T", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -472,6 +549,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 
