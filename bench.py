@@ -532,7 +532,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
-    ap.add_argument("--cpu-sample", type=int, default=480)
+    ap.add_argument("--cpu-sample", type=int, default=1600)
     ap.add_argument("--ref-sample", type=int, default=160)
     ap.add_argument("--locations", type=int, default=0,
                     help="use only the first K locations (small case for profiling)")

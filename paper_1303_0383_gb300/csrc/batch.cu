@@ -114,6 +114,7 @@ BatchLaunch make_launch(const Plan &P, int32_t method, int32_t precision, int64_
   b.pmax = P.pmax;
   b.Mmax = P.Mmax;
   b.mean = mean; b.s2 = s2; b.var = var; b.idx = idx; b.status = status;
+  b.idx_total = P.idx_total;
   b.ctas_per_sm = ctas;
   return b;
 }

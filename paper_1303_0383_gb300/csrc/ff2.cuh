@@ -60,17 +60,35 @@ __device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
   return fast_two_sum2(sub2(f2s(0.0f), np), e);
 }
 
-// acc - a*b with the same scalar multiplier a for both lanes (see ff_sub_prod_acc); the
-// caller passes a and its negation (nah = -a.h) so that no sign flip is needed per term.
-__device__ __forceinline__ ff2 ff2_sub_prod_acc(ff2 acc, float2 ah, float2 nah, float2 al,
-                                                float2 bh, float2 bl) {
-  const float2 np = mul2(nah, bh);        // -p
-  float2 e = fma2(ah, bh, np);            // a.h b.h - p
+// Compensated accumulation of acc - sum_i a_i b_i for float-float a_i (the same for both
+// lanes) and pairs b_i: the running sum h is plain FP32; the rounding error of every
+// addition (TwoSum, exact) and of every product (TwoProd with the cross terms a_h b_l and
+// a_l b_h) is collected in a second FP32 sum l, and h + l is renormalised once at the end.
+// This is the Dot2 scheme of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005), whose result is as accurate as the sum computed in twice
+// the working precision and then rounded, extended to float-float operands.  Per term: 12
+// packed instructions, and only one addition on each loop-carried chain.
+// The caller passes a_h as (a_h, a_h, -a_h, -a_h) and a_l as (a_l, a_l): no sign flips or
+// register moves are needed per term.
+struct ff2acc {
+  float2 h, l;
+};
+
+__device__ __forceinline__ void ff2acc_sub_prod(ff2acc &acc, float4 ahn, float2 al, float4 b) {
+  const float2 ah = make_float2(ahn.x, ahn.y), nah = make_float2(ahn.z, ahn.w);
+  const float2 bh = make_float2(b.x, b.y), bl = make_float2(b.z, b.w);
+  const float2 np = mul2(nah, bh);                 // -p, p = rn(a_h b_h)
+  float2 e = fma2(ah, bh, np);                     // a_h b_h - p, exact
   e = fma2(ah, bl, e);
-  e = fma2(al, bh, e);                    // a b - p (to float precision)
-  const ff2 s = two_sum2(acc.h, np);      // acc.h - p
-  return fast_two_sum2(s.h, sub2(add2(s.l, acc.l), e));
+  e = fma2(al, bh, e);                             // a b - p to FP32 accuracy
+  const float2 s = add2(acc.h, np);                // TwoSum(h, -p)
+  const float2 bb = sub2(s, acc.h);
+  const float2 err = add2(sub2(acc.h, sub2(s, bb)), sub2(np, bb));
+  acc.l = add2(acc.l, sub2(err, e));
+  acc.h = s;
 }
+
+__device__ __forceinline__ ff2 ff2acc_result(ff2acc acc) { return two_sum2(acc.h, acc.l); }
 
 __device__ __forceinline__ ff ff2_x(ff2 a) { return ff{a.h.x, a.l.x}; }
 __device__ __forceinline__ ff ff2_y(ff2 a) { return ff{a.h.y, a.l.y}; }

@@ -7,6 +7,7 @@
 #include <atomic>
 
 #include "lagp.h"
+#include "batch.cuh"
 
 namespace lagp {
 
@@ -33,7 +34,6 @@ int dev_info(DevInfo *out);
 size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms);
 int knn_launch(const double *X, int64_t N, int32_t p, const double *XX, int64_t T, int32_t ncand,
                int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream);
-struct LocDesc;
 int knn_launch_list(const double *X, int64_t N, int32_t p, const double *XX, int64_t nloc,
                     int32_t M, int32_t *cand, void *ws, size_t ws_bytes, cudaStream_t stream,
                     const int32_t *list, const LocDesc *locs, int ldxx, int ctas_per_sm);
@@ -66,6 +66,24 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
 size_t select_mixed_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
 int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+// Kernel (c) on a selected design: FP64 predictive equations for every location from its
+// design indices (idx < 0 marks a location whose screen failed).
+struct PredictArgs {
+  const double *X, *Z;
+  int32_t p;
+  const double *XX;
+  int64_t T;
+  int32_t n, nmax;
+  double theta, g;
+  const int32_t *idx;
+  BatchView B;  // per-location tables, or designs == nullptr for a uniform launch
+  double *mean, *s2, *var;
+  int8_t *status;
+};
+size_t predict_fp64_workspace_bytes(int64_t T, int32_t nmax, int num_sms);
+int predict_fp64_launch(const PredictArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+int predict_fp64_prepare();
+
 // MSPE variant of kernels (b)+(c), FP64.
 size_t select_mspe_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
 int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
@@ -85,6 +103,7 @@ struct BatchLaunch {
   int32_t nmax, pmax, Mmax;
   double *mean, *s2, *var;
   int32_t *idx;                // location t's indices at locs[t].idx_off
+  int64_t idx_total;           // sum of the locations' n (the length of idx)
   int8_t *status;
   int32_t ctas_per_sm;         // 1 .. select_max_ctas()
 };

@@ -12,10 +12,11 @@
 //           the top 12 bits of d2f (non-negative floats order like their bit patterns);
 //   select  a block scan finds the bin b* holding the ncand-th smallest d2f; tau is the
 //           upper edge of b*;
-//   pass 2  d2f recomputed (bit-identical); every point with d2f <= tau + 2E survives, where E bounds |d2f - d2| (FP32
-//           rounding of the coordinates, the differences and the fused sum; see
-//           fp32_err_bound) -- all true members survive; survivors get their exact FP64
-//           d2 and go to shared memory;
+//   pass 2  d2f recomputed (bit-identical); every point with d2f <= tau + 2E survives, where
+//           E bounds |d2f - d2| (FP32 rounding of the coordinates, the differences and the
+//           fused sum; see fp32_err_bound) -- all true members survive; the survivors are
+//           listed in shared memory and then get their exact FP64 d2 from that list, so
+//           the FP64 work runs on full warps;
 //   sort    bitonic sort of the survivors by (d2 bits, index); the first ncand indices
 //           are written out.
 // If the survivors do not fit in shared memory (many points tied at the boundary), the
@@ -312,17 +313,23 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     }
     __syncthreads();
     const float thr = sh_thr;
-    // pass 2: the same FP32 distances again (bit for bit); survivors get exact FP64 ones
+    // pass 2: the same FP32 distances again (bit for bit); survivors are listed first
     for (int i = threadIdx.x; i < N; i += KB) {
       const float d2f = sqdist_f32<P>(xf, Xf + (size_t)i * p, p);
       if (d2f <= thr) {
-        const double d2 = sqdist_exact(xs, X + (size_t)i * p, p);
         const uint32_t pos = atomicAdd(&sh_count, 1u);
-        if (pos < (uint32_t)cap) put_key(kh, kl, sidx, pos, d2, i);
+        if (pos < (uint32_t)cap) sidx[pos] = i;
       }
     }
     __syncthreads();
     int cnt = (int)sh_count;
+    // then get their exact FP64 distances from the compacted list: a warp instruction of
+    // the FP64 pipe serves 32 survivors instead of the few a strided pass would hold
+    if (cnt <= cap)
+      for (int r = threadIdx.x; r < cnt; r += KB) {
+        const int32_t i = sidx[r];
+        put_key(kh, kl, sidx, (uint32_t)r, sqdist_exact(xs, X + (size_t)i * p, p), i);
+      }
     __syncthreads();
     if (cnt > cap || cnt < M)  // too many ties at the boundary (or, defensively, too few)
       cnt = knn_exact_location(X, N, p, M, xs, kh, kl, sidx, hist, cap, warp_tmp, &sh_bin,

@@ -1,0 +1,242 @@
+// predict.cu -- kernel (c) for a screen that returns only the local design: the FP64
+// predictive equations on the selected design of every location.
+//
+// Gramacy & Apley, Sec. 2, Eqs. predgp and preds2: with K_n = K(X_n, X_n) + g I,
+// k(x) = K(X_n, x) and psi = Y^T K_n^{-1} Y,
+//   mu(x) = k(x)^T K_n^{-1} Y,   s2(x) = psi (K(x, x) + g - k(x)^T K_n^{-1} k(x)) / n,
+// and var = psi (K(x, x) + g - k(x)^T K_n^{-1} k(x)) / (n - 2), the variance of the
+// Student-t predictive.  [K_n | k(x) | Y] is factored by a right-looking Cholesky, which
+// makes for every entry the same subtractions, in the same order, as the row-by-row
+// factorisation followed by forward substitution (u_x = L^{-1} k(x), y~ = L^{-1} Y):
+// v_n(x) = 1 + g - |u_x|^2 is a cancellation whose rounding error is of the order of the
+// tolerance, and keeping the textbook operation order keeps this kernel's rounding close
+// to that of a plain sequential evaluation.
+// FP64 runs at 1/64 of the FP32 rate on this GPU, so every FP64 instruction is kept busy
+// on all lanes: the matrix entries and each step's trailing update are flattened over
+// the threads; a division by the pivot is a product with its reciprocal plus one
+// correction (Markstein: with the correctly rounded reciprocal y of b and q = rn(a y),
+// q + (a - b q) y gives the correctly rounded a / b), and the pivot's square root and
+// reciprocal are taken by the thread that finishes the pivot, so a step costs two block
+// barriers.
+//
+// One CTA owns one location at a time (persistent CTAs over a work queue); the matrix
+// lives in shared memory when it fits, else in a per-CTA slot of the workspace.
+#include <math.h>
+
+#include "batch.cuh"
+#include "fp64_exp.cuh"
+#include "internal.h"
+
+namespace lagp {
+namespace {
+
+constexpr int PB = 128;              // threads per CTA
+constexpr size_t kSmemA = 48 * 1024; // largest matrix kept in shared memory
+
+struct PredParams {
+  const double *X, *Z;
+  int p;
+  const double *XX;
+  int64_t T;
+  int n, nmax;
+  double theta, g;
+  const int32_t *idx;     // selected design indices (location t's n at its offset)
+  BatchView B;
+  double *mean, *s2, *var;
+  int8_t *status;
+  double *Ag;             // per-CTA matrix slots when the matrix is not in shared memory
+  int a_in_smem;
+  int *queue;
+};
+
+__device__ __forceinline__ double corr(const double *a, const double *b, int p, double theta_inv,
+                                       const double *etab) {
+  double acc = 0.0;
+  for (int k = 0; k < p; k++) {
+    const double t = a[k] - b[k];
+    acc = fma(t, t, acc);
+  }
+  return exp_nonpos(-acc * theta_inv, etab);
+}
+
+// Row t of the lower triangle {(a, b): 0 <= b <= a} holding flat entry e.
+__device__ __forceinline__ int tri_row(int e) {
+  int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (a * (a + 1) / 2 > e) a--;
+  while ((a + 1) * (a + 2) / 2 <= e) a++;
+  return a;
+}
+
+__global__ void __launch_bounds__(PB) predict_fp64_kernel(PredParams P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nmax = P.nmax;
+  double *rl = reinterpret_cast<double *>(smraw);     // nmax: 1 / l_kk
+  double *A = P.a_in_smem ? rl + nmax : P.Ag + (size_t)blockIdx.x * nmax * (nmax + 2);
+  __shared__ double etab[64];
+  __shared__ double xl[kMaxP];
+  __shared__ int sh_loc, sh_fail;
+  const int tid = threadIdx.x;
+  if (tid < 64) etab[tid] = c_exp.tab[tid];
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) sh_loc = atomicAdd(P.queue, 1);
+    __syncthreads();
+    if (sh_loc >= P.T) break;
+    const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, 0, 0, P.theta, P.g,
+                                    P.idx, const_cast<int32_t *>(P.idx));
+    const int64_t loc = L.loc;
+    const int n = L.n, p = L.p, lda = n + 2;
+    const int32_t *d = L.idx;  // design indices of this location
+    if (tid < p) xl[tid] = L.x[tid];
+    if (tid == 0) sh_fail = d[0] < 0;  // the screen failed for this location
+    __syncthreads();
+    if (!sh_fail) {
+      // K_n + g I (lower triangle), k(x) and Y
+      const int ntri = n * (n + 1) / 2;
+      for (int e = tid; e < ntri + 2 * n; e += PB) {
+        if (e < ntri) {
+          const int a = tri_row(e), b = e - a * (a + 1) / 2;
+          const double *xa = L.X + (int64_t)d[a] * p;
+          A[a * lda + b] = (a == b) ? L.onepg
+                                    : corr(xa, L.X + (int64_t)d[b] * p, p, L.theta_inv, etab);
+        } else {
+          const int a = (e - ntri) >> 1, col = (e - ntri) & 1;
+          A[a * lda + n + col] = col == 0 ? corr(L.X + (int64_t)d[a] * p, xl, p, L.theta_inv, etab)
+                                          : L.Z[d[a]];
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double d0 = A[0];
+        if (!(d0 > 0.0)) sh_fail = 1;
+        const double l0 = sqrt(d0);
+        A[0] = l0;
+        rl[0] = 1.0 / l0;
+      }
+      __syncthreads();
+      for (int k = 0; k < n && !sh_fail; k++) {
+        const double lkk = A[k * lda + k], r = rl[k];
+        // column k and the extra columns of row k divided by the pivot
+        for (int i = k + 1 + tid; i < n + 2; i += PB) {
+          double *ap = (i < n) ? &A[i * lda + k] : &A[k * lda + i];
+          const double a = *ap, q = a * r;
+          *ap = fma(fma(-q, lkk, a), r, q);
+        }
+        __syncthreads();
+        // a_il -= l_ik l_lk for k < l <= i, and the extra columns: b_i -= l_ik b_k
+        const int rows = n - k - 1, ntr = rows * (rows + 1) / 2;
+        for (int e = tid; e < ntr + 2 * rows; e += PB) {
+          if (e < ntr) {
+            const int t = tri_row(e), c = e - t * (t + 1) / 2;
+            const int i = k + 1 + t, l = k + 1 + c;
+            const double v = fma(-A[i * lda + k], A[l * lda + k], A[i * lda + l]);
+            if (e == 0) {  // the next pivot is final: its square root and reciprocal
+              if (!(v > 0.0)) sh_fail = 1;
+              const double lv = sqrt(v);
+              A[i * lda + l] = lv;
+              rl[k + 1] = 1.0 / lv;
+            } else {
+              A[i * lda + l] = v;
+            }
+          } else {
+            const int i = k + 1 + ((e - ntr) >> 1), col = (e - ntr) & 1;
+            A[i * lda + n + col] = fma(-A[i * lda + k], A[k * lda + n + col], A[i * lda + n + col]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (sh_fail) {
+        P.mean[loc] = NAN;
+        P.s2[loc] = NAN;
+        if (P.var) P.var[loc] = NAN;
+        if (P.status) P.status[loc] = (int8_t)LAGP_ERR_NOT_PD;
+      } else {
+        // in index order, as a sequential evaluation of the sums
+        double mu = 0.0, psi = 0.0, vx = L.onepg;
+        for (int i = 0; i < n; i++) {
+          const double ux = A[i * lda + n], yt = A[i * lda + n + 1];
+          mu = fma(ux, yt, mu);
+          psi = fma(yt, yt, psi);
+          vx = fma(-ux, ux, vx);
+        }
+        const double pv = psi * vx;
+        P.mean[loc] = mu;
+        P.s2[loc] = pv / n;
+        if (P.var) P.var[loc] = pv / (n - 2);
+        if (P.status) P.status[loc] = 0;
+      }
+    }
+  }
+}
+
+bool a_fits_smem(int nmax) { return (size_t)nmax * (nmax + 2) * sizeof(double) <= kSmemA; }
+
+size_t pred_smem_bytes(int nmax) {
+  return (size_t)nmax * sizeof(double) +
+         (a_fits_smem(nmax) ? (size_t)nmax * (nmax + 2) * sizeof(double) : 0);
+}
+
+int pred_grid(int64_t T, int nmax, const DevInfo &di) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, predict_fp64_kernel, PB,
+                                                    pred_smem_bytes(nmax)) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t g = (int64_t)di.num_sms * per_sm;
+  return (int)(T < g ? (T > 0 ? T : 1) : g);
+}
+
+// Worst-case grid for sizing the workspace before the occupancy is known: the smem limit
+// alone allows at most this many CTAs of 128 threads per SM (2048 threads per SM).
+int pred_grid_bound(int64_t T, int num_sms) {
+  const int64_t g = (int64_t)num_sms * 16;
+  return (int)(T < g ? (T > 0 ? T : 1) : g);
+}
+
+}  // namespace
+
+size_t predict_fp64_workspace_bytes(int64_t T, int32_t nmax, int num_sms) {
+  size_t b = 256;
+  if (!a_fits_smem(nmax))
+    b += align_up((size_t)pred_grid_bound(T, num_sms) * nmax * (nmax + 2) * sizeof(double), 256);
+  return b;
+}
+
+int predict_fp64_launch(const PredictArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
+  if (a.T == 0) return LAGP_OK;
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st) return st;
+  st = exp_table_upload();  // this translation unit's copy of the exp constants
+  if (st) return st;
+  if (ws_bytes < predict_fp64_workspace_bytes(a.T, a.nmax, di.num_sms)) return LAGP_ERR_INVALID_ARG;
+  const size_t smem = pred_smem_bytes(a.nmax);
+  cudaError_t e = cudaFuncSetAttribute(predict_fp64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  int G = pred_grid(a.T, a.nmax, di);
+  const int Gb = pred_grid_bound(a.T, di.num_sms);
+  if (G > Gb) G = Gb;
+  char *w = static_cast<char *>(ws);
+  PredParams P;
+  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.n = a.n; P.nmax = a.nmax;
+  P.theta = a.theta; P.g = a.g; P.idx = a.idx;
+  P.B = a.B;
+  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.status = a.status;
+  P.queue = reinterpret_cast<int *>(w);
+  P.a_in_smem = a_fits_smem(a.nmax) ? 1 : 0;
+  P.Ag = P.a_in_smem ? nullptr : reinterpret_cast<double *>(w + 256);
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  predict_fp64_kernel<<<G, PB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  return cuda_status(cudaGetLastError());
+}
+
+int predict_fp64_prepare() { return exp_table_upload(); }
+
+}  // namespace lagp

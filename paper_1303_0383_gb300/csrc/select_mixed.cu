@@ -19,11 +19,10 @@
 // step needs one block barrier: every thread merges the per-warp best/second-best results
 // and derives the step's pivot scalars itself.
 //
-// After the last step the predictive equations (Eqs. predgp, preds2) are evaluated in
-// FP64 on the final design: K_n augmented with the columns k(x) and Y is factored by a
-// right-looking Cholesky, which performs for every entry the same subtractions in the
-// same order as the row-by-row factorisation and forward substitution, so mu, s2 and V
-// carry FP64 accuracy whatever precision screened the candidates.
+// The kernel returns the selected design of every location; the predictive equations
+// (Eqs. predgp, preds2) are then evaluated in FP64 on that design by kernel (c) in
+// predict.cu, so mu, s2 and V carry FP64 accuracy whatever precision screened the
+// candidates.
 #include <math.h>
 
 #include "ff.cuh"
@@ -49,9 +48,7 @@ struct MixParams {
   int nmax, pmax;  // slot dimensions (the largest n and p of the launch)
   double theta, theta_inv, g, onepg;
   BatchView B;     // per-location tables (B.designs == nullptr: uniform launch)
-  double *mean, *s2, *var;
-  int32_t *idx;
-  int8_t *status;
+  int32_t *idx;   // selected design indices (required: the caller's or the workspace's)
   float4 *U;     // slots of n x Qpad candidate pairs: row j of every candidate's factor row
   float4 *Xr;    // slots of p x Qpad pairs: candidate coordinates minus x
   double *A;     // slots of n x (n + 2): FP64 factorisation
@@ -165,6 +162,87 @@ __device__ __forceinline__ double corr64(const double *a, const double *b, int p
   return exp_nonpos(-acc * theta_inv, etab);
 }
 
+// One step of the screen for NP candidate pairs of this thread (Sec. 3.2 update, in
+// float-float): K(s, c) from the squared distance, the new factor entry
+// u_c[j] = (K(s, c) - u_s . u_c) / L_jj, then v_{j+1}(c) = v_j(c) - u_c[j]^2,
+// cov_{j+1}(x, c) = cov_j(x, c) - u_x[j] u_c[j], and the ALC screen score cov^2 / v.
+struct StepCtx {
+  float4 *U;
+  const float4 *Xr;
+  float4 *vp, *cp;
+  const float4 *srow4;
+  const float2 *srow2, *sxs;
+  const float *tabh, *tabl;
+  ff2 inv2, uxj2, thinv2;
+  int Qpad, p, j;
+  bool want;
+};
+
+template <int NP>
+__device__ __forceinline__ void screen_pairs(const StepCtx &C, const int (&qs)[NP],
+                                             const unsigned char *used, float &b1, int &r1,
+                                             float &b2) {
+  ff2acc acc[NP];
+#pragma unroll
+  for (int h = 0; h < NP; h++) {
+    const int q = qs[h];
+    // squared distance of the pair to the new point
+    float2 dh = f2s(0.0f), dl = f2s(0.0f);
+    for (int k = 0; k < C.p; k++) {
+      const ff2 b = ff2_load(C.Xr + k * C.Qpad + q);
+      const float2 a = C.sxs[k];
+      const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
+      const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
+      const float2 ph = mul2(df.h, df.h);
+      const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
+      const ff2 sacc = two_sum2(dh, ph);
+      dh = sacc.h;
+      dl = add2(add2(sacc.l, dl), pl);
+    }
+    const ff2 d2 = fast_two_sum2(dh, dl);
+    const ff2 arg = ff2_mul(d2, C.thinv2);
+    const ff2 kc = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, C.tabh, C.tabl);   // K(s, c)
+    acc[h] = ff2acc{kc.h, kc.l};
+  }
+  // K(s, c) - sum_i u_s[i] u_c[i]: compensated accumulation, the pairs interleaved (four
+  // loads of U in flight either way)
+  const float4 *Uq[NP];
+#pragma unroll
+  for (int h = 0; h < NP; h++) Uq[h] = C.U + qs[h];
+  constexpr int UNR = 4 / NP;
+#pragma unroll UNR
+  for (int i = 0; i < C.j; i++) {
+    const float4 a = C.srow4[i];
+    const float2 al = C.srow2[i];
+    float4 b[NP];
+#pragma unroll
+    for (int h = 0; h < NP; h++) b[h] = Uq[h][(size_t)i * C.Qpad];
+#pragma unroll
+    for (int h = 0; h < NP; h++) ff2acc_sub_prod(acc[h], a, al, b[h]);
+  }
+#pragma unroll
+  for (int h = 0; h < NP; h++) {
+    const int q = qs[h];
+    const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+    const ff2 u = ff2_mul(ff2acc_result(acc[h]), C.inv2);           // u_c[j]
+    ff2_store(C.U + (size_t)C.j * C.Qpad + q, u);
+    const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
+    ff2 v = ff2_sub(v0, ff2_mul(u, u));
+    ff2 cx = ff2_sub(c0, ff2_mul(C.uxj2, u));
+    // A used lane keeps its values: the step's pivot may be the partner of a live
+    // candidate, and other threads read the pivot's v and cov at the start of the step
+    // without a barrier after it.
+    if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
+    if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
+    ff2_store(C.vp + q, v);
+    ff2_store(C.cp + q, cx);
+    if (C.want) {
+      if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), 2 * q, b1, r1, b2);
+      if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), 2 * q + 1, b1, r1, b2);
+    }
+  }
+}
+
 #ifndef LAGP_MIX_MINB
 #define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM: 85 registers, no spills
 #endif
@@ -173,8 +251,12 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
   const int Qpad = P.Qpad, nmax = P.nmax;
   float4 *vp = reinterpret_cast<float4 *>(smraw);            // Qpad: v_j(c) pairs
   float4 *cp = vp + Qpad;                                    // Qpad: cov_j(x, c) pairs
-  float2 *wrow = reinterpret_cast<float2 *>(cp + Qpad);      // (MB/32) x (nmax + kMaxP): per-warp s row
-  int *dr = reinterpret_cast<int *>(wrow + (MB / 32) * (nmax + kMaxP));  // nmax
+  // per-warp copies of the new factor row: {h, h, -h, -h} and {l, l} per entry
+  const int nrow = (nmax + 1) & ~1;
+  float4 *wrow4 = reinterpret_cast<float4 *>(cp + Qpad);     // (MB/32) x nrow
+  float2 *wrow2 = reinterpret_cast<float2 *>(wrow4 + (MB / 32) * nrow);  // (MB/32) x nrow
+  float2 *wxs = wrow2 + (MB / 32) * nrow;                    // (MB/32) x kMaxP: new point
+  int *dr = reinterpret_cast<int *>(wxs + (MB / 32) * kMaxP);  // nmax
   int *rlist = dr + nmax;                                    // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   __shared__ float tabh[64], tabl[64];
@@ -195,8 +277,9 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
   float4 *Xr = P.Xr + (size_t)blockIdx.x * P.pmax * Qpad;
   const int lda = nmax + 2;
   double *A = P.A + (size_t)blockIdx.x * nmax * lda;
-  float2 *srow = wrow + warp * (nmax + kMaxP);  // this warp's copy of the new factor row
-  float2 *sxs = srow + nmax;                    // and of the new point's coordinates
+  float4 *srow4 = wrow4 + warp * nrow;  // this warp's copy of the new factor row
+  float2 *srow2 = wrow2 + warp * nrow;
+  float2 *sxs = wxs + warp * kMaxP;     // and of the new point's coordinates
 
   for (;;) {
     __syncthreads();
@@ -205,7 +288,6 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     if (sh_loc >= P.T) break;
     const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, P.M, P.n0, P.theta,
                                     P.g, P.cand, P.idx);
-    const int64_t loc = L.loc;
     const int n = L.n, p = L.p, M = L.M;
     const int32_t *cnd = L.cand;
     const ff onepg = ff_from_double(L.onepg);
@@ -267,7 +349,8 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       // this warp's copy of the new factor row u_s and of x_s (relative to x)
       for (int i = lane; i < j; i += 32) {
         const ff u = ff2_get(U + (size_t)i * Qpad, s);
-        srow[i] = make_float2(u.h, u.l);
+        srow4[i] = make_float4(u.h, u.h, -u.h, -u.h);
+        srow2[i] = f2s(u.l);
       }
       if (lane < p) {
         const ff xk = ff2_get(Xr + lane * Qpad, s);
@@ -280,49 +363,13 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       const ff2 thinv2{f2s(thinv.h), f2s(thinv.l)};
       float b1 = -1.0f, b2 = -1.0f;
       int r1 = 0x7fffffff;
+      const StepCtx C{U, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2, thinv2, Qpad, p, j, want};
+      // one pair at a time (interleaving two pairs per thread measured slower: the extra
+      // loads in flight only add L2 pressure)
       for (int q = tid; q < Q; q += MB) {
-        const bool u0 = used[2 * q], u1 = used[2 * q + 1];
-        if (u0 && u1) continue;
-        // squared distance of the pair to the new point
-        float2 dh = f2s(0.0f), dl = f2s(0.0f);
-        for (int k = 0; k < p; k++) {
-          const ff2 b = ff2_load(Xr + k * Qpad + q);
-          const float2 a = sxs[k];
-          const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
-          const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
-          const float2 ph = mul2(df.h, df.h);
-          const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
-          const ff2 sacc = two_sum2(dh, ph);
-          dh = sacc.h;
-          dl = add2(add2(sacc.l, dl), pl);
-        }
-        const ff2 d2 = fast_two_sum2(dh, dl);
-        const ff2 arg = ff2_mul(d2, thinv2);
-        ff2 t = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, tabh, tabl);   // K(s, c)
-        const float4 *Uq = U + q;
-#pragma unroll 4
-        for (int i = 0; i < j; i++, Uq += Qpad) {
-          const float2 sr = srow[i];
-          const float4 uv = *Uq;
-          t = ff2_sub_prod_acc(t, f2s(sr.x), f2s(-sr.x), f2s(sr.y), make_float2(uv.x, uv.y),
-                               make_float2(uv.z, uv.w));
-        }
-        const ff2 u = ff2_mul(t, inv2);                            // u_c[j]
-        ff2_store(U + (size_t)j * Qpad + q, u);
-        const ff2 v0 = ff2_load(vp + q), c0 = ff2_load(cp + q);
-        ff2 v = ff2_sub(v0, ff2_mul(u, u));
-        ff2 cx = ff2_sub(c0, ff2_mul(uxj2, u));
-        // A used lane keeps its values: the step's pivot may be the partner of a live
-        // candidate, and other threads read the pivot's v and cov at the start of the
-        // step without a barrier after it.
-        if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
-        if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
-        ff2_store(vp + q, v);
-        ff2_store(cp + q, cx);
-        if (want) {
-          if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), 2 * q, b1, r1, b2);
-          if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), 2 * q + 1, b1, r1, b2);
-        }
+        if (used[2 * q] && used[2 * q + 1]) continue;
+        const int qs[1] = {q};
+        screen_pairs<1>(C, qs, used, b1, r1, b2);
       }
       // best and second-best screen scores: warp shuffles, one barrier, then every
       // thread merges the per-warp results itself (double-buffered by step parity)
@@ -436,46 +483,9 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       best = sh_rbest;
     }
     __syncthreads();
-    if (!sh_fail) {
-      // FP64 predictive equations on the final design: factor [K_n | k(x) | Y]
-      for (int qq = tid; qq < n * (n + 2); qq += MB) {
-        const int a = qq / (n + 2), b = qq % (n + 2);
-        if (b < n && b > a) continue;  // only the lower triangle is read
-        const double *xa = L.X + (int64_t)cnd[dr[a]] * p;
-        double val;
-        if (b < n) val = (a == b) ? L.onepg : corr64(xa, L.X + (int64_t)cnd[dr[b]] * p, p, L.theta_inv, etab);
-        else if (b == n) val = corr64(xa, xl, p, L.theta_inv, etab);
-        else val = L.Z[cnd[dr[a]]];
-        A[a * lda + b] = val;
-      }
-      __syncthreads();
-      chol_aug_fp64(A, n, lda, 2, &sh_fail);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      if (sh_fail) {
-        if (P.status) P.status[loc] = (int8_t)LAGP_ERR_NOT_PD;
-        P.mean[loc] = NAN;
-        P.s2[loc] = NAN;
-        if (P.var) P.var[loc] = NAN;
-      } else {
-        double mu = 0.0, psi = 0.0, vx = L.onepg;
-        for (int i = 0; i < n; i++) {
-          const double ux = A[i * lda + n], yt = A[i * lda + n + 1];
-          mu = fma(ux, yt, mu);
-          psi = fma(yt, yt, psi);
-          vx = fma(-ux, ux, vx);
-        }
-        const double pv = psi * vx;
-        P.mean[loc] = mu;
-        P.s2[loc] = pv / n;
-        if (P.var) P.var[loc] = pv / (n - 2);
-        if (P.status) P.status[loc] = 0;
-      }
-    }
-    if (L.idx) {
-      for (int i = tid; i < n; i += MB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
-    }
+    // the design (design indices), or -1 when a step failed; kernel (c) (predict.cu)
+    // evaluates the predictive equations on it in FP64
+    for (int i = tid; i < n; i += MB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
   }
 }
 
@@ -488,28 +498,64 @@ int mix_mpad(int M) { return (int)align_up((size_t)M, 64); }
 
 size_t mix_smem_bytes(int Mpad, int n) {
   const size_t Qpad = (size_t)Mpad / 2;
-  return Qpad * 2 * sizeof(float4) + (size_t)(MB / 32) * (n + kMaxP) * sizeof(float2) +
+  const size_t nrow = (size_t)((n + 1) & ~1);
+  return Qpad * 2 * sizeof(float4) +
+         (size_t)(MB / 32) * (nrow * (sizeof(float4) + sizeof(float2)) + kMaxP * sizeof(float2)) +
          (size_t)n * sizeof(int) + RESCORE_CAP * sizeof(int) + align_up((size_t)Mpad, 16);
 }
 
 struct MixLayout {
-  size_t u, xr, a, total;
+  size_t u, xr, a, idx, pred, total;
 };
 
-MixLayout mix_layout(int G, int p, int n, int M) {
+// [queue | re-score counter | U | Xr | A | design indices | kernel (c) workspace]
+MixLayout mix_layout(int G, int p, int n, int M, int64_t T, int64_t idx_total, int num_sms) {
   const size_t Qpad = (size_t)mix_mpad(M) / 2;
   MixLayout L;
   L.u = align_up((size_t)G * n * Qpad * sizeof(float4), 256);
   L.xr = align_up((size_t)G * p * Qpad * sizeof(float4), 256);
   L.a = align_up((size_t)G * n * (n + 2) * sizeof(double), 256);
-  L.total = 256 + 256 + L.u + L.xr + L.a;
+  L.idx = align_up((size_t)idx_total * sizeof(int32_t), 256);
+  L.pred = predict_fp64_workspace_bytes(T, n, num_sms);
+  L.total = 256 + 256 + L.u + L.xr + L.a + L.idx + L.pred;
   return L;
+}
+
+// The screen, then kernel (c) on the designs it selected.
+int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, char *w,
+            int32_t *user_idx, const DevInfo &di, cudaStream_t stream) {
+  P.queue = reinterpret_cast<int *>(w);
+  P.rescores = reinterpret_cast<int *>(w + 256);
+  char *o = w + 512;
+  P.U = reinterpret_cast<float4 *>(o);
+  o += L.u;
+  P.Xr = reinterpret_cast<float4 *>(o);
+  o += L.xr;
+  P.A = reinterpret_cast<double *>(o);
+  o += L.a;
+  // the design goes to the caller's idx, or to the workspace when the caller wants none
+  P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(o);
+  o += L.idx;
+  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_mixed_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(w, 0, 512, stream);  // work counter and re-score counter
+  if (e != cudaSuccess) return cuda_status(e);
+  select_mixed_kernel<<<G, MB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  PredictArgs pa = pa_in;
+  pa.idx = P.idx;
+  return predict_fp64_launch(pa, o, L.pred, stream);
 }
 
 }  // namespace
 
 size_t select_mixed_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms) {
-  return mix_layout(mix_grid(T, num_sms), p, n, ncand).total;
+  return mix_layout(mix_grid(T, num_sms), p, n, ncand, T, T * n, num_sms).total;
 }
 
 int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
@@ -520,35 +566,25 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   st = exp_table_upload();
   if (st) return st;
   const int G = mix_grid(a.T, di.num_sms);
-  const MixLayout L = mix_layout(G, a.p, a.n, a.M);
+  const MixLayout L = mix_layout(G, a.p, a.n, a.M, a.T, a.T * a.n, di.num_sms);
   if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
-  char *w = static_cast<char *>(ws);
   MixParams P;
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = mix_mpad(a.M); P.Qpad = P.Mpad / 2; P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
   P.B = BatchView{nullptr, nullptr, nullptr, 0};
-  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
-  P.queue = reinterpret_cast<int *>(w);
-  P.rescores = reinterpret_cast<int *>(w + 256);
-  P.U = reinterpret_cast<float4 *>(w + 512);
-  P.Xr = reinterpret_cast<float4 *>(w + 512 + L.u);
-  P.A = reinterpret_cast<double *>(w + 512 + L.u + L.xr);
-  const size_t smem = mix_smem_bytes(P.Mpad, a.n);
-  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(select_mixed_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemsetAsync(w, 0, 512, stream);  // work counter and re-score counter
-  if (e != cudaSuccess) return cuda_status(e);
-  select_mixed_kernel<<<G, MB, smem, stream>>>(P);
-  g_launches.fetch_add(1);
-  return cuda_status(cudaGetLastError());
+  PredictArgs pa;
+  pa.X = a.X; pa.Z = a.Z; pa.p = a.p; pa.XX = a.XX; pa.T = a.T; pa.n = a.n; pa.nmax = a.n;
+  pa.theta = a.theta; pa.g = a.g; pa.idx = nullptr; pa.B = P.B;
+  pa.mean = a.mean; pa.s2 = a.s2; pa.var = a.var; pa.status = a.status;
+  return mix_run(P, pa, L, G, static_cast<char *>(ws), a.idx, di, stream);
 }
 
 size_t select_mixed_batch_workspace_bytes(const BatchLaunch &b, int G) {
-  return mix_layout(G, b.pmax, b.nmax, b.Mmax).total;
+  DevInfo di;
+  const int sms = dev_info(&di) == LAGP_OK ? di.num_sms : 152;
+  return mix_layout(G, b.pmax, b.nmax, b.Mmax, b.T, b.idx_total, sms).total;
 }
 
 int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G,
@@ -558,33 +594,24 @@ int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, i
   if (st) return st;
   st = exp_table_upload();  // this translation unit's copy of the exp constants
   if (st) return st;
-  const MixLayout L = mix_layout(G, b.pmax, b.nmax, b.Mmax);
+  const MixLayout L = mix_layout(G, b.pmax, b.nmax, b.Mmax, b.T, b.idx_total, di.num_sms);
   if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
-  char *w = static_cast<char *>(ws);
   MixParams P;
   P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
   P.M = b.Mmax; P.Mpad = mix_mpad(b.Mmax); P.Qpad = P.Mpad / 2; P.n0 = 0; P.n = b.nmax;
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;
   P.B = BatchView{b.designs, b.locs, b.order, b.ldxx};
-  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
-  P.queue = reinterpret_cast<int *>(w);
-  P.rescores = reinterpret_cast<int *>(w + 256);
-  P.U = reinterpret_cast<float4 *>(w + 512);
-  P.Xr = reinterpret_cast<float4 *>(w + 512 + L.u);
-  P.A = reinterpret_cast<double *>(w + 512 + L.u + L.xr);
-  const size_t smem = mix_smem_bytes(P.Mpad, b.nmax);
-  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(select_mixed_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemsetAsync(w, 0, 512, stream);
-  if (e != cudaSuccess) return cuda_status(e);
-  select_mixed_kernel<<<G, MB, smem, stream>>>(P);
-  g_launches.fetch_add(1);
-  return cuda_status(cudaGetLastError());
+  PredictArgs pa;
+  pa.X = nullptr; pa.Z = nullptr; pa.p = b.pmax; pa.XX = b.XX; pa.T = b.T; pa.n = b.nmax;
+  pa.nmax = b.nmax; pa.theta = 1.0; pa.g = 0.0; pa.idx = nullptr; pa.B = P.B;
+  pa.mean = b.mean; pa.s2 = b.s2; pa.var = b.var; pa.status = b.status;
+  return mix_run(P, pa, L, G, static_cast<char *>(ws), b.idx, di, stream);
 }
 
-int select_mixed_prepare() { return exp_table_upload(); }
+int select_mixed_prepare() {
+  const int st = exp_table_upload();
+  return st ? st : predict_fp64_prepare();
+}
 
 }  // namespace lagp
