@@ -39,6 +39,9 @@ int dev_info(DevInfo *out) {
     e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_status(e);
     d.smem_optin = (size_t)v;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    d.smem_per_sm = (size_t)v;
     cache[dev] = d;
     have[dev] = true;
   }

@@ -27,6 +27,7 @@ struct DevInfo {
   int device;
   int num_sms;
   size_t smem_optin;
+  size_t smem_per_sm;
 };
 int dev_info(DevInfo *out);
 

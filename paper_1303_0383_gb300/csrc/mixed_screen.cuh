@@ -1,0 +1,343 @@
+// mixed_screen.cuh -- device code of the mixed-precision screen (select_mixed.cu): the
+// float-float exp, the per-pair step, score tracking and the FP64 re-score.
+//
+// Gramacy & Apley, Sec. 3: the greedy local design adds the candidate that maximises the
+// ALC reduction cov_j(x,c)^2 / v_j(c) (Eq. dxy; SM Eq. dxy2); Sec. 3.2 gives the O(j)
+// update of every candidate's quantities when the design grows by one point.
+// Included by one translation unit each: c_exp is that unit's copy of the exp constants.
+#pragma once
+
+#include <math.h>
+
+#include "ff.cuh"
+#include "ff2.cuh"
+#include "fp64_exp.cuh"
+#include "internal.h"
+
+namespace lagp {
+namespace {
+
+constexpr float DELTA = 1e-5f;     // near-tie margin for the FP64 re-score
+constexpr int RESCORE_CAP = 64;    // candidates re-scored per pass
+
+// exp(a) for a <= 0 on a pair, in float-float (Tang's table-driven method with N = 64, see
+// fp64_exp.cuh): a = k ln2/64 + r, exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 with
+// the first two terms in float-float and the rest in FP32 (they are below 3e-8).
+// Arguments below -87 give 0.
+__device__ __forceinline__ ff2 exp_ff2(ff2 a, const float *tabh, const float *tabl) {
+  const float2 ah = make_float2(fmaxf(a.h.x, -87.0f), fmaxf(a.h.y, -87.0f));
+  const float2 magic = f2s(12582912.0f);  // 1.5 * 2^23
+  const float2 t = fma2(ah, f2s(c_exp.inv_ln2_64f), magic);
+  const float2 kf = sub2(t, magic);
+  const int kx = __float_as_int(t.x) - 0x4B400000, ky = __float_as_int(t.y) - 0x4B400000;
+  const float2 r1 = fma2(neg2(kf), f2s(c_exp.c1), ah);  // exact
+  const float2 p2h = mul2(kf, f2s(c_exp.c2));
+  const float2 p2l = fma2(kf, f2s(c_exp.c2), neg2(p2h));
+  const ff2 s = two_sum2(r1, neg2(p2h));
+  const float2 rl = add2(sub2(sub2(s.l, p2l), mul2(kf, f2s(c_exp.c3))), a.l);
+  const ff2 r = fast_two_sum2(s.h, rl);
+  const float2 sqh = mul2(r.h, r.h);
+  const float2 sql = fma2(add2(r.h, r.h), r.l, fma2(r.h, r.h, neg2(sqh)));
+  const float2 P = mul2(mul2(r.h, sqh),
+                        fma2(r.h, fma2(r.h, f2s(1.0f / 120.0f), f2s(1.0f / 24.0f)), f2s(1.0f / 6.0f)));
+  const ff2 e = two_sum2(r.h, mul2(f2s(0.5f), sqh));
+  const ff2 E = fast_two_sum2(e.h, add2(add2(e.l, r.l), fma2(f2s(0.5f), sql, P)));
+  const float2 Th = f2(tabh[kx & 63], tabh[ky & 63]), Tl = f2(tabl[kx & 63], tabl[ky & 63]);
+  const float2 ph = mul2(Th, E.h);
+  const float2 pl = fma2(Th, E.h, neg2(ph));
+  const ff2 s2 = two_sum2(Th, ph);
+  const float2 low = add2(add2(s2.l, pl), fma2(Th, E.l, fma2(Tl, E.h, Tl)));
+  const ff2 res = fast_two_sum2(s2.h, low);
+  const float2 sc = f2(__int_as_float(((kx >> 6) + 127) << 23), __int_as_float(((ky >> 6) + 127) << 23));
+  ff2 out{mul2(res.h, sc), mul2(res.l, sc)};
+  if (a.h.x < -87.0f) out.h.x = out.l.x = 0.0f;
+  if (a.h.y < -87.0f) out.h.y = out.l.y = 0.0f;
+  return out;
+}
+
+__device__ __forceinline__ bool frac_better(double a, double da, int ra, double b, double db,
+                                            int rb) {
+  const double l = a * db, r = b * da;
+  return l > r || (l == r && ra < rb);
+}
+
+// Screen score comparison: larger score, ties to the smaller rank.
+__device__ __forceinline__ void track2(float sc, int c, float &b1, int &r1, float &b2) {
+  if (sc > b1 || (sc == b1 && c < r1)) {
+    b2 = b1;
+    b1 = sc;
+    r1 = c;
+  } else if (sc > b2) {
+    b2 = sc;
+  }
+}
+
+__device__ __forceinline__ void merge2(float o1, int orr, float o2, float &b1, int &r1, float &b2) {
+  if (o1 > b1 || (o1 == b1 && orr < r1)) {
+    b2 = fmaxf(b1, o2);
+    b1 = o1;
+    r1 = orr;
+  } else {
+    b2 = fmaxf(b2, o1);
+  }
+}
+
+// Right-looking FP64 Cholesky of the j x j design matrix held in A (row-major, leading
+// dimension lda) together with naug extra columns (forward substitution of them).  The
+// matrix entries are built by the caller.  Sets *fail on a pivot <= 0.
+__device__ void chol_aug_fp64(double *A, int j, int lda, int naug, int *fail) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < j; k++) {
+    if (tid == 0) {
+      const double d = A[k * lda + k];
+      if (!(d > 0.0)) *fail = 1;
+      A[k * lda + k] = sqrt(d);
+    }
+    __syncthreads();
+    if (*fail) return;
+    const double lkk = A[k * lda + k];
+    for (int i = k + 1 + tid; i < j; i += nt) A[i * lda + k] = A[i * lda + k] / lkk;
+    if (tid < naug) A[k * lda + j + tid] = A[k * lda + j + tid] / lkk;
+    __syncthreads();
+    const int w = j - k - 1 + naug;
+    const int rows = j - k - 1;
+    for (int q = tid; q < rows * w; q += nt) {
+      const int ii = k + 1 + q / w;
+      const int ll = q % w;
+      if (ll < rows) {
+        const int l = k + 1 + ll;
+        if (l <= ii) A[ii * lda + l] = fma(-A[ii * lda + k], A[l * lda + k], A[ii * lda + l]);
+      } else {
+        const int a = ll - rows;
+        A[ii * lda + j + a] = fma(-A[ii * lda + k], A[k * lda + j + a], A[ii * lda + j + a]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double corr64(const double *a, const double *b, int p, double theta_inv,
+                                         const double *etab) {
+  double acc = 0.0;
+  for (int k = 0; k < p; k++) {
+    const double t = a[k] - b[k];
+    acc = fma(t, t, acc);
+  }
+  return exp_nonpos(-acc * theta_inv, etab);
+}
+
+// One step of the screen for NP candidate pairs of this thread (Sec. 3.2 update, in
+// float-float): K(s, c) from the squared distance, the new factor entry
+// u_c[j] = (K(s, c) - u_s . u_c) / L_jj, then v_{j+1}(c) = v_j(c) - u_c[j]^2,
+// cov_{j+1}(x, c) = cov_j(x, c) - u_x[j] u_c[j], and the ALC screen score cov^2 / v.
+struct StepCtx {
+  float4 *U;     // factor rows in global memory (rows R .. n-1 are used)
+  float4 *Us;    // the first R rows, in shared memory
+  int R;
+  const float4 *Xr;
+  float4 *vp, *cp;
+  const float4 *srow4;
+  const float2 *srow2, *sxs;
+  const float *tabh, *tabl;
+  ff2 inv2, uxj2, thinv2;
+  int Qpad, p, j;
+  int c0;        // global rank of the first candidate held here
+  bool want;
+};
+
+template <int NP>
+__device__ __forceinline__ void screen_pairs(const StepCtx &C, const int (&qs)[NP],
+                                             const unsigned char *used, float &b1, int &r1,
+                                             float &b2) {
+  ff2acc acc[NP];
+#pragma unroll
+  for (int h = 0; h < NP; h++) {
+    const int q = qs[h];
+    // squared distance of the pair to the new point
+    float2 dh = f2s(0.0f), dl = f2s(0.0f);
+    for (int k = 0; k < C.p; k++) {
+      const ff2 b = ff2_load(C.Xr + k * C.Qpad + q);
+      const float2 a = C.sxs[k];
+      const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
+      const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
+      const float2 ph = mul2(df.h, df.h);
+      const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
+      const ff2 sacc = two_sum2(dh, ph);
+      dh = sacc.h;
+      dl = add2(add2(sacc.l, dl), pl);
+    }
+    const ff2 d2 = fast_two_sum2(dh, dl);
+    const ff2 arg = ff2_mul(d2, C.thinv2);
+    const ff2 kc = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, C.tabh, C.tabl);   // K(s, c)
+    acc[h] = ff2acc{kc.h, kc.l};
+  }
+  // K(s, c) - sum_i u_s[i] u_c[i]: compensated accumulation over the rows held in shared
+  // memory, then over those in global memory (four loads of U in flight either way)
+  constexpr int UNR = 4 / NP;
+  const int jr = C.j < C.R ? C.j : C.R;
+#pragma unroll UNR
+  for (int i = 0; i < jr; i++) {
+    const float4 a = C.srow4[i];
+    const float2 al = C.srow2[i];
+    float4 b[NP];
+#pragma unroll
+    for (int h = 0; h < NP; h++) b[h] = C.Us[(size_t)i * C.Qpad + qs[h]];
+#pragma unroll
+    for (int h = 0; h < NP; h++) ff2acc_sub_prod(acc[h], a, al, b[h]);
+  }
+#pragma unroll UNR
+  for (int i = jr; i < C.j; i++) {
+    const float4 a = C.srow4[i];
+    const float2 al = C.srow2[i];
+    float4 b[NP];
+#pragma unroll
+    for (int h = 0; h < NP; h++) b[h] = C.U[(size_t)i * C.Qpad + qs[h]];
+#pragma unroll
+    for (int h = 0; h < NP; h++) ff2acc_sub_prod(acc[h], a, al, b[h]);
+  }
+#pragma unroll
+  for (int h = 0; h < NP; h++) {
+    const int q = qs[h];
+    const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+    const ff2 u = ff2_mul(ff2acc_result(acc[h]), C.inv2);           // u_c[j]
+    ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
+    const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
+    ff2 v = ff2_sub(v0, ff2_mul(u, u));
+    ff2 cx = ff2_sub(c0, ff2_mul(C.uxj2, u));
+    // A used lane keeps its values: the step's pivot may be the partner of a live
+    // candidate, and other threads read the pivot's v and cov at the start of the step
+    // without a barrier after it.
+    if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
+    if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
+    ff2_store(C.vp + q, v);
+    ff2_store(C.cp + q, cx);
+    if (C.want) {
+      if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), C.c0 + 2 * q, b1, r1, b2);
+      if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), C.c0 + 2 * q + 1, b1, r1, b2);
+    }
+  }
+}
+
+// ---- FP64 re-score of near-tied candidates (Sec. 3.3 decisions in FP64) ----
+// Scratch and inputs of one CTA's re-score pass.  The CTA holds candidates with global
+// ranks c0 .. c0 + Mloc - 1 (local index c = rank - c0); the current design is dr[0..jd)
+// (global ranks), its FP64 factor is formed in A (global memory, jd x (jd + 1)).
+struct RescoreCtx {
+  const double *X;
+  const int32_t *cnd;          // the location's candidate list (global ranks -> design rows)
+  const double *xl;            // x (shared memory)
+  const double *etab;
+  const unsigned char *used;   // local flags
+  const float4 *vp, *cp;       // local screen state (pairs)
+  const int *dr;
+  double *A;
+  int *rlist, *nlist, *fail;
+  double *red_n, *red_d;
+  int *red_rr;
+  int p, c0, Mloc, jd, lda;
+  double theta_inv, onepg;
+};
+
+// Every candidate of this CTA whose screen score is within 2 DELTA of B1 is re-scored in
+// FP64: the design's FP64 Cholesky factor (with k(x) as an extra column) is formed from
+// scratch, and each listed candidate's u = L^{-1} k_c is obtained by forward substitution
+// (one warp per candidate), giving v_j(c) = 1 + g - |u|^2 and cov_j(x, c) = k(x, c) - u.u_x.
+// On return (all threads, after a barrier): *bn / *bd is the CTA's best FP64 score as a
+// fraction, *br its global rank (0x7fffffff if none), or *R.fail set (factor not PD).
+__device__ void rescore_fp64(const RescoreCtx &R, float B1, double *bn_out, double *bd_out,
+                             int *br_out) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int jd = R.jd, lda = R.lda, p = R.p;
+  if (tid == 0) *R.nlist = 0;
+  __syncthreads();
+  for (int c = tid; c < R.Mloc; c += nt) {
+    if (R.used[c]) continue;
+    const ff v = ff2_get(R.vp, c), cx = ff2_get(R.cp, c);
+    if (!(v.h > 0.0f)) continue;
+    const float sc = __fdiv_rn(cx.h * cx.h, v.h);
+    if (sc >= B1 * (1.0f - 2.0f * DELTA)) {
+      const int pos = atomicAdd(R.nlist, 1);
+      if (pos < RESCORE_CAP) R.rlist[pos] = c;
+    }
+  }
+  // FP64 factor of the current design with k(x) as an extra column (lower triangle)
+  for (int qq = tid; qq < jd * (jd + 1); qq += nt) {
+    const int a = qq / (jd + 1), b = qq % (jd + 1);
+    if (b < jd && b > a) continue;
+    const double *xa = R.X + (int64_t)R.cnd[R.dr[a]] * p;
+    double val;
+    if (b < jd) val = (a == b) ? R.onepg : corr64(xa, R.X + (int64_t)R.cnd[R.dr[b]] * p, p, R.theta_inv, R.etab);
+    else val = corr64(xa, R.xl, p, R.theta_inv, R.etab);
+    R.A[a * lda + b] = val;
+  }
+  __syncthreads();
+  chol_aug_fp64(R.A, jd, lda, 1, R.fail);
+  if (*R.fail) return;
+  const double *A = R.A;
+  // more near-ties than the list holds: re-score every remaining candidate
+  const bool all = *R.nlist > RESCORE_CAP;
+  const int nl = all ? R.Mloc : *R.nlist;
+  double bn = -1.0, bd = 1.0;
+  int br = 0x7fffffff;
+  for (int item = warp; item < nl; item += nt / 32) {
+    const int c = all ? item : R.rlist[item];
+    if (R.used[c]) continue;
+    const int rank = R.c0 + c;
+    const double *xc = R.X + (int64_t)R.cnd[rank] * p;
+    double tv[kMaxN / 32];
+#pragma unroll
+    for (int r = 0; r < kMaxN / 32; r++) {
+      const int i = 32 * r + lane;
+      tv[r] = (i < jd) ? corr64(R.X + (int64_t)R.cnd[R.dr[i]] * p, xc, p, R.theta_inv, R.etab) : 0.0;
+    }
+    double vsum = R.onepg;
+    double cov = corr64(R.xl, xc, p, R.theta_inv, R.etab);
+    for (int m = 0; m < jd; m++) {
+      double own = 0.0;
+#pragma unroll
+      for (int r = 0; r < kMaxN / 32; r++)
+        if (32 * r + lane == m) own = tv[r];
+      const double um_l = own / A[m * lda + m];
+      const double um = __shfl_sync(0xffffffffu, um_l, m & 31);
+      vsum = fma(-um, um, vsum);
+      cov = fma(-A[m * lda + jd], um, cov);
+#pragma unroll
+      for (int r = 0; r < kMaxN / 32; r++) {
+        const int i = 32 * r + lane;
+        if (i > m && i < jd) tv[r] = fma(-A[i * lda + m], um, tv[r]);
+      }
+    }
+    if (vsum > 0.0) {
+      const double num = cov * cov;
+      if (frac_better(num, vsum, rank, bn, bd, br)) {
+        bn = num;
+        bd = vsum;
+        br = rank;
+      }
+    }
+  }
+  if (lane == 0) {
+    R.red_n[warp] = bn;
+    R.red_d[warp] = bd;
+    R.red_rr[warp] = br;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < nt / 32; w++)
+      if (frac_better(R.red_n[w], R.red_d[w], R.red_rr[w], bn, bd, br)) {
+        bn = R.red_n[w];
+        bd = R.red_d[w];
+        br = R.red_rr[w];
+      }
+    R.red_n[0] = bn;
+    R.red_d[0] = bd;
+    R.red_rr[0] = br;
+  }
+  __syncthreads();
+  *bn_out = R.red_n[0];
+  *bd_out = R.red_d[0];
+  *br_out = R.red_rr[0];
+}
+
+}  // namespace
+}  // namespace lagp

@@ -25,18 +25,13 @@
 // candidates.
 #include <math.h>
 
-#include "ff.cuh"
-#include "ff2.cuh"
 #include "batch.cuh"
-#include "fp64_exp.cuh"
-#include "internal.h"
+#include "mixed_screen.cuh"
 
 namespace lagp {
 namespace {
 
 constexpr int MB = 256;            // threads per CTA
-constexpr float DELTA = 1e-5f;     // near-tie margin for the FP64 re-score
-constexpr int RESCORE_CAP = 64;    // candidates re-scored per pass
 
 struct MixParams {
   const double *X, *Z;
@@ -50,201 +45,15 @@ struct MixParams {
   BatchView B;     // per-location tables (B.designs == nullptr: uniform launch)
   int32_t *idx;   // selected design indices (required: the caller's or the workspace's)
   float4 *U;     // slots of n x Qpad candidate pairs: row j of every candidate's factor row
+  int R;         // rows 0 .. R-1 live in shared memory instead
   float4 *Xr;    // slots of p x Qpad pairs: candidate coordinates minus x
   double *A;     // slots of n x (n + 2): FP64 factorisation
   int *queue;
   int *rescores; // count of FP64 re-score passes (diagnostics)
 };
 
-// exp(a) for a <= 0 on a pair, in float-float (Tang's table-driven method with N = 64, see
-// fp64_exp.cuh): a = k ln2/64 + r, exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 with
-// the first two terms in float-float and the rest in FP32 (they are below 3e-8).
-// Arguments below -87 give 0.
-__device__ __forceinline__ ff2 exp_ff2(ff2 a, const float *tabh, const float *tabl) {
-  const float2 ah = make_float2(fmaxf(a.h.x, -87.0f), fmaxf(a.h.y, -87.0f));
-  const float2 magic = f2s(12582912.0f);  // 1.5 * 2^23
-  const float2 t = fma2(ah, f2s(c_exp.inv_ln2_64f), magic);
-  const float2 kf = sub2(t, magic);
-  const int kx = __float_as_int(t.x) - 0x4B400000, ky = __float_as_int(t.y) - 0x4B400000;
-  const float2 r1 = fma2(neg2(kf), f2s(c_exp.c1), ah);  // exact
-  const float2 p2h = mul2(kf, f2s(c_exp.c2));
-  const float2 p2l = fma2(kf, f2s(c_exp.c2), neg2(p2h));
-  const ff2 s = two_sum2(r1, neg2(p2h));
-  const float2 rl = add2(sub2(sub2(s.l, p2l), mul2(kf, f2s(c_exp.c3))), a.l);
-  const ff2 r = fast_two_sum2(s.h, rl);
-  const float2 sqh = mul2(r.h, r.h);
-  const float2 sql = fma2(add2(r.h, r.h), r.l, fma2(r.h, r.h, neg2(sqh)));
-  const float2 P = mul2(mul2(r.h, sqh),
-                        fma2(r.h, fma2(r.h, f2s(1.0f / 120.0f), f2s(1.0f / 24.0f)), f2s(1.0f / 6.0f)));
-  const ff2 e = two_sum2(r.h, mul2(f2s(0.5f), sqh));
-  const ff2 E = fast_two_sum2(e.h, add2(add2(e.l, r.l), fma2(f2s(0.5f), sql, P)));
-  const float2 Th = f2(tabh[kx & 63], tabh[ky & 63]), Tl = f2(tabl[kx & 63], tabl[ky & 63]);
-  const float2 ph = mul2(Th, E.h);
-  const float2 pl = fma2(Th, E.h, neg2(ph));
-  const ff2 s2 = two_sum2(Th, ph);
-  const float2 low = add2(add2(s2.l, pl), fma2(Th, E.l, fma2(Tl, E.h, Tl)));
-  const ff2 res = fast_two_sum2(s2.h, low);
-  const float2 sc = f2(__int_as_float(((kx >> 6) + 127) << 23), __int_as_float(((ky >> 6) + 127) << 23));
-  ff2 out{mul2(res.h, sc), mul2(res.l, sc)};
-  if (a.h.x < -87.0f) out.h.x = out.l.x = 0.0f;
-  if (a.h.y < -87.0f) out.h.y = out.l.y = 0.0f;
-  return out;
-}
-
-__device__ __forceinline__ bool frac_better(double a, double da, int ra, double b, double db,
-                                            int rb) {
-  const double l = a * db, r = b * da;
-  return l > r || (l == r && ra < rb);
-}
-
-// Screen score comparison: larger score, ties to the smaller rank.
-__device__ __forceinline__ void track2(float sc, int c, float &b1, int &r1, float &b2) {
-  if (sc > b1 || (sc == b1 && c < r1)) {
-    b2 = b1;
-    b1 = sc;
-    r1 = c;
-  } else if (sc > b2) {
-    b2 = sc;
-  }
-}
-
-__device__ __forceinline__ void merge2(float o1, int orr, float o2, float &b1, int &r1, float &b2) {
-  if (o1 > b1 || (o1 == b1 && orr < r1)) {
-    b2 = fmaxf(b1, o2);
-    b1 = o1;
-    r1 = orr;
-  } else {
-    b2 = fmaxf(b2, o1);
-  }
-}
-
-// Right-looking FP64 Cholesky of the j x j design matrix held in A (row-major, leading
-// dimension lda) together with naug extra columns (forward substitution of them).  The
-// matrix entries are built by the caller.  Sets *fail on a pivot <= 0.
-__device__ void chol_aug_fp64(double *A, int j, int lda, int naug, int *fail) {
-  const int tid = threadIdx.x;
-  for (int k = 0; k < j; k++) {
-    if (tid == 0) {
-      const double d = A[k * lda + k];
-      if (!(d > 0.0)) *fail = 1;
-      A[k * lda + k] = sqrt(d);
-    }
-    __syncthreads();
-    if (*fail) return;
-    const double lkk = A[k * lda + k];
-    for (int i = k + 1 + tid; i < j; i += MB) A[i * lda + k] = A[i * lda + k] / lkk;
-    if (tid < naug) A[k * lda + j + tid] = A[k * lda + j + tid] / lkk;
-    __syncthreads();
-    const int w = j - k - 1 + naug;
-    const int rows = j - k - 1;
-    for (int q = tid; q < rows * w; q += MB) {
-      const int ii = k + 1 + q / w;
-      const int ll = q % w;
-      if (ll < rows) {
-        const int l = k + 1 + ll;
-        if (l <= ii) A[ii * lda + l] = fma(-A[ii * lda + k], A[l * lda + k], A[ii * lda + l]);
-      } else {
-        const int a = ll - rows;
-        A[ii * lda + j + a] = fma(-A[ii * lda + k], A[k * lda + j + a], A[ii * lda + j + a]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ double corr64(const double *a, const double *b, int p, double theta_inv,
-                                         const double *etab) {
-  double acc = 0.0;
-  for (int k = 0; k < p; k++) {
-    const double t = a[k] - b[k];
-    acc = fma(t, t, acc);
-  }
-  return exp_nonpos(-acc * theta_inv, etab);
-}
-
-// One step of the screen for NP candidate pairs of this thread (Sec. 3.2 update, in
-// float-float): K(s, c) from the squared distance, the new factor entry
-// u_c[j] = (K(s, c) - u_s . u_c) / L_jj, then v_{j+1}(c) = v_j(c) - u_c[j]^2,
-// cov_{j+1}(x, c) = cov_j(x, c) - u_x[j] u_c[j], and the ALC screen score cov^2 / v.
-struct StepCtx {
-  float4 *U;
-  const float4 *Xr;
-  float4 *vp, *cp;
-  const float4 *srow4;
-  const float2 *srow2, *sxs;
-  const float *tabh, *tabl;
-  ff2 inv2, uxj2, thinv2;
-  int Qpad, p, j;
-  bool want;
-};
-
-template <int NP>
-__device__ __forceinline__ void screen_pairs(const StepCtx &C, const int (&qs)[NP],
-                                             const unsigned char *used, float &b1, int &r1,
-                                             float &b2) {
-  ff2acc acc[NP];
-#pragma unroll
-  for (int h = 0; h < NP; h++) {
-    const int q = qs[h];
-    // squared distance of the pair to the new point
-    float2 dh = f2s(0.0f), dl = f2s(0.0f);
-    for (int k = 0; k < C.p; k++) {
-      const ff2 b = ff2_load(C.Xr + k * C.Qpad + q);
-      const float2 a = C.sxs[k];
-      const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
-      const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
-      const float2 ph = mul2(df.h, df.h);
-      const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
-      const ff2 sacc = two_sum2(dh, ph);
-      dh = sacc.h;
-      dl = add2(add2(sacc.l, dl), pl);
-    }
-    const ff2 d2 = fast_two_sum2(dh, dl);
-    const ff2 arg = ff2_mul(d2, C.thinv2);
-    const ff2 kc = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, C.tabh, C.tabl);   // K(s, c)
-    acc[h] = ff2acc{kc.h, kc.l};
-  }
-  // K(s, c) - sum_i u_s[i] u_c[i]: compensated accumulation, the pairs interleaved (four
-  // loads of U in flight either way)
-  const float4 *Uq[NP];
-#pragma unroll
-  for (int h = 0; h < NP; h++) Uq[h] = C.U + qs[h];
-  constexpr int UNR = 4 / NP;
-#pragma unroll UNR
-  for (int i = 0; i < C.j; i++) {
-    const float4 a = C.srow4[i];
-    const float2 al = C.srow2[i];
-    float4 b[NP];
-#pragma unroll
-    for (int h = 0; h < NP; h++) b[h] = Uq[h][(size_t)i * C.Qpad];
-#pragma unroll
-    for (int h = 0; h < NP; h++) ff2acc_sub_prod(acc[h], a, al, b[h]);
-  }
-#pragma unroll
-  for (int h = 0; h < NP; h++) {
-    const int q = qs[h];
-    const bool u0 = used[2 * q], u1 = used[2 * q + 1];
-    const ff2 u = ff2_mul(ff2acc_result(acc[h]), C.inv2);           // u_c[j]
-    ff2_store(C.U + (size_t)C.j * C.Qpad + q, u);
-    const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
-    ff2 v = ff2_sub(v0, ff2_mul(u, u));
-    ff2 cx = ff2_sub(c0, ff2_mul(C.uxj2, u));
-    // A used lane keeps its values: the step's pivot may be the partner of a live
-    // candidate, and other threads read the pivot's v and cov at the start of the step
-    // without a barrier after it.
-    if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
-    if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
-    ff2_store(C.vp + q, v);
-    ff2_store(C.cp + q, cx);
-    if (C.want) {
-      if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), 2 * q, b1, r1, b2);
-      if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), 2 * q + 1, b1, r1, b2);
-    }
-  }
-}
-
 #ifndef LAGP_MIX_MINB
-#define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM: 85 registers, no spills
+#define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM, each with its first factor rows in shared memory
 #endif
 __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -256,9 +65,11 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
   float4 *wrow4 = reinterpret_cast<float4 *>(cp + Qpad);     // (MB/32) x nrow
   float2 *wrow2 = reinterpret_cast<float2 *>(wrow4 + (MB / 32) * nrow);  // (MB/32) x nrow
   float2 *wxs = wrow2 + (MB / 32) * nrow;                    // (MB/32) x kMaxP: new point
-  int *dr = reinterpret_cast<int *>(wxs + (MB / 32) * kMaxP);  // nmax
-  int *rlist = dr + nmax;                                    // RESCORE_CAP
+  int *dr = reinterpret_cast<int *>(wxs + (MB / 32) * kMaxP);  // nmax (padded to 4)
+  int *rlist = dr + ((nmax + 3) & ~3);                       // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
+  float4 *Us = reinterpret_cast<float4 *>(used + P.Mpad);    // R x Qpad: first factor rows
+  const int R = P.R;
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
   __shared__ double xl[kMaxP];
@@ -266,7 +77,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
   __shared__ int red_r1[2][MB / 32];
   __shared__ double red_n[MB / 32], red_d[MB / 32];
   __shared__ int red_rr[MB / 32];
-  __shared__ int sh_loc, sh_fail, sh_nlist, sh_rbest;
+  __shared__ int sh_loc, sh_fail, sh_nlist;
   if (threadIdx.x < 64) {
     tabh[threadIdx.x] = c_exp.tabf_h[threadIdx.x];
     tabl[threadIdx.x] = c_exp.tabf_l[threadIdx.x];
@@ -348,7 +159,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       if (tid == ((s >> 1) % MB)) used[s] = 1;  // the pair's owner keeps the flags
       // this warp's copy of the new factor row u_s and of x_s (relative to x)
       for (int i = lane; i < j; i += 32) {
-        const ff u = ff2_get(U + (size_t)i * Qpad, s);
+        const ff u = ff2_get((i < R ? Us : U) + (size_t)i * Qpad, s);
         srow4[i] = make_float4(u.h, u.h, -u.h, -u.h);
         srow2[i] = f2s(u.l);
       }
@@ -363,7 +174,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       const ff2 thinv2{f2s(thinv.h), f2s(thinv.l)};
       float b1 = -1.0f, b2 = -1.0f;
       int r1 = 0x7fffffff;
-      const StepCtx C{U, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2, thinv2, Qpad, p, j, want};
+      const StepCtx C{U, Us, R, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2, thinv2, Qpad, p, j, 0, want};
       // one pair at a time (interleaving two pairs per thread measured slower: the extra
       // loads in flight only add L2 pressure)
       for (int q = tid; q < Q; q += MB) {
@@ -394,93 +205,14 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       const bool near = R1 != 0x7fffffff && B2 >= B1 * (1.0f - DELTA);
       if (!near) continue;
       // ---- FP64 re-score of the near-tied candidates (rare) ----
-      if (tid == 0) {
-        sh_nlist = 0;
-        if (P.rescores) atomicAdd(P.rescores, 1);
-      }
-      __syncthreads();
-      const int jd = j + 1;  // design size now
-      for (int c = tid; c < M; c += MB) {
-        if (used[c]) continue;
-        const ff v = ff2_get(vp, c), cx = ff2_get(cp, c);
-        if (!(v.h > 0.0f)) continue;
-        const float sc = __fdiv_rn(cx.h * cx.h, v.h);
-        if (sc >= B1 * (1.0f - 2.0f * DELTA)) {
-          const int pos = atomicAdd(&sh_nlist, 1);
-          if (pos < RESCORE_CAP) rlist[pos] = c;
-        }
-      }
-      // FP64 factor of the current design with k(x) as an extra column (lower triangle)
-      for (int qq = tid; qq < jd * (jd + 1); qq += MB) {
-        const int a = qq / (jd + 1), b = qq % (jd + 1);
-        if (b < jd && b > a) continue;
-        const double *xa = L.X + (int64_t)cnd[dr[a]] * p;
-        double val;
-        if (b < jd) val = (a == b) ? L.onepg : corr64(xa, L.X + (int64_t)cnd[dr[b]] * p, p, L.theta_inv, etab);
-        else val = corr64(xa, xl, p, L.theta_inv, etab);
-        A[a * lda + b] = val;
-      }
-      __syncthreads();
-      chol_aug_fp64(A, jd, lda, 1, &sh_fail);
+      if (tid == 0 && P.rescores) atomicAdd(P.rescores, 1);
+      const RescoreCtx R{L.X, cnd, xl, etab, used, vp, cp, dr, A, rlist, &sh_nlist, &sh_fail,
+                         red_n, red_d, red_rr, p, 0, M, j + 1, lda, L.theta_inv, L.onepg};
+      double bn, bd;
+      int br;
+      rescore_fp64(R, B1, &bn, &bd, &br);
       if (sh_fail) break;
-      // more near-ties than the list holds: re-score every remaining candidate
-      const bool all = sh_nlist > RESCORE_CAP;
-      const int nl = all ? M : sh_nlist;
-      double bn = -1.0, bd = 1.0;
-      int br = 0x7fffffff;
-      for (int item = warp; item < nl; item += MB / 32) {
-        const int c = all ? item : rlist[item];
-        if (used[c]) continue;
-        const double *xc = L.X + (int64_t)cnd[c] * p;
-        double tv[kMaxN / 32];
-#pragma unroll
-        for (int r = 0; r < kMaxN / 32; r++) {
-          const int i = 32 * r + lane;
-          tv[r] = (i < jd) ? corr64(L.X + (int64_t)cnd[dr[i]] * p, xc, p, L.theta_inv, etab) : 0.0;
-        }
-        double vsum = L.onepg;
-        double cov = corr64(xl, xc, p, L.theta_inv, etab);
-        for (int m = 0; m < jd; m++) {
-          double own = 0.0;
-#pragma unroll
-          for (int r = 0; r < kMaxN / 32; r++)
-            if (32 * r + lane == m) own = tv[r];
-          const double um_l = own / A[m * lda + m];
-          const double um = __shfl_sync(0xffffffffu, um_l, m & 31);
-          vsum = fma(-um, um, vsum);
-          cov = fma(-A[m * lda + jd], um, cov);
-#pragma unroll
-          for (int r = 0; r < kMaxN / 32; r++) {
-            const int i = 32 * r + lane;
-            if (i > m && i < jd) tv[r] = fma(-A[i * lda + m], um, tv[r]);
-          }
-        }
-        if (vsum > 0.0) {
-          const double num = cov * cov;
-          if (frac_better(num, vsum, c, bn, bd, br)) {
-            bn = num;
-            bd = vsum;
-            br = c;
-          }
-        }
-      }
-      if (lane == 0) {
-        red_n[warp] = bn;
-        red_d[warp] = bd;
-        red_rr[warp] = br;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        for (int w = 1; w < MB / 32; w++)
-          if (frac_better(red_n[w], red_d[w], red_rr[w], bn, bd, br)) {
-            bn = red_n[w];
-            bd = red_d[w];
-            br = red_rr[w];
-          }
-        sh_rbest = (br != 0x7fffffff) ? br : best;
-      }
-      __syncthreads();
-      best = sh_rbest;
+      best = (br != 0x7fffffff) ? br : best;
     }
     __syncthreads();
     // the design (design indices), or -1 when a step failed; kernel (c) (predict.cu)
@@ -496,12 +228,31 @@ int mix_grid(int64_t T, int num_sms) {
 
 int mix_mpad(int M) { return (int)align_up((size_t)M, 64); }
 
-size_t mix_smem_bytes(int Mpad, int n) {
+// Dynamic shared memory: the per-candidate state, then the first R factor rows.  Mpad is
+// a multiple of 64, so the rows start 16-byte aligned.
+size_t mix_smem_bytes(int Mpad, int n, int R) {
   const size_t Qpad = (size_t)Mpad / 2;
   const size_t nrow = (size_t)((n + 1) & ~1);
   return Qpad * 2 * sizeof(float4) +
          (size_t)(MB / 32) * (nrow * (sizeof(float4) + sizeof(float2)) + kMaxP * sizeof(float2)) +
-         (size_t)n * sizeof(int) + RESCORE_CAP * sizeof(int) + align_up((size_t)Mpad, 16);
+         (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + (size_t)Mpad +
+         (size_t)R * Qpad * sizeof(float4);
+}
+
+// Factor rows kept in shared memory: as many as LAGP_MIX_MINB resident CTAs per SM leave
+// room for (the rest stream from L2).  Row i is read at every step after step i, so the
+// first rows carry the most traffic.
+int mix_rows_in_smem(int Mpad, int n, const DevInfo &di) {
+  cudaFuncAttributes fa;
+  size_t stat = 4096;
+  if (cudaFuncGetAttributes(&fa, select_mixed_kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+  size_t per_cta = di.smem_per_sm / LAGP_MIX_MINB;
+  const size_t fixed = stat + 1024 + mix_smem_bytes(Mpad, n, 0);  // 1 KB reserved per CTA
+  if (per_cta > di.smem_optin) per_cta = di.smem_optin;
+  if (per_cta <= fixed) return 0;
+  const size_t row = (size_t)Mpad / 2 * sizeof(float4);
+  const size_t r = (per_cta - fixed) / row;
+  return (int)(r < (size_t)n ? r : (size_t)n);
 }
 
 struct MixLayout {
@@ -536,7 +287,8 @@ int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, ch
   // the design goes to the caller's idx, or to the workspace when the caller wants none
   P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(o);
   o += L.idx;
-  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax);
+  P.R = mix_rows_in_smem(P.Mpad, P.nmax, di);
+  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax, P.R);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
   cudaError_t e = cudaFuncSetAttribute(select_mixed_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
