@@ -135,8 +135,10 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v == "Active"})
+        counts = {nm: sum(1 for r in rows if r[2][i] == "Active") for i, nm in enumerate(names)}
         return {"sm_mhz": statistics.median(r[0] for r in rows),
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "reason_samples": {k: v for k, v in counts.items() if v},
                 "samples": len(rows), "power_w_max": max(r[3] for r in rows)}
 
 

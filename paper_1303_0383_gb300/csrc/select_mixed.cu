@@ -218,6 +218,14 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     // the design (design indices), or -1 when a step failed; kernel (c) (predict.cu)
     // evaluates the predictive equations on it in FP64
     for (int i = tid; i < n; i += MB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
+    // The factor rows in global memory are dead now (the next location rewrites each row
+    // before reading it): drop their L2 lines without writing them back to DRAM.
+    {
+      char *u0 = reinterpret_cast<char *>(U + (size_t)R * Qpad);
+      const int nlines = (int)(((size_t)(n > R ? n - R : 0) * Qpad * sizeof(float4)) / 128);
+      for (int l = tid; l < nlines; l += MB)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(u0 + (size_t)l * 128) : "memory");
+    }
   }
 }
 
