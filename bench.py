@@ -71,15 +71,21 @@ FP32_PEAK_TOPS_DERIVED = 152 * 128 * 2.07e9 / 1e12   # SMs x FP32 lanes/clk x ma
 
 def mixed_fp32_ops_per_location(n0, n, M, p):
     """FP32 operations (add, multiply or fused multiply-add, each one) of the float-float
-    screen for one location: every pool candidate at step j costs 15j (the float-float
-    row dot: TwoProd with cross terms, TwoSum, renormalisation) + 20p + 3 (squared
-    distance) + 11 (scaling by 1/theta) + 66 (float-float exponential) + 9 (new row entry)
-    + 42 (v and cov updates) + 6 (screen score)."""
+    screen for one location: every pool candidate at step j costs 12j + 6 (the compensated
+    row dot: TwoProd with cross terms and TwoSum per term, one renormalisation) + 20p + 3
+    (squared distance) + 11 (scaling by 1/theta) + 66 (float-float exponential) + 9 (new
+    row entry) + 42 (v and cov updates) + 6 (screen score)."""
     total = 0
     for j in range(n - 1):
         pool = M - (j + 1)
-        total += pool * (15 * j + 20 * p + 3 + 11 + 66 + 9 + 42 + 6)
+        total += pool * (12 * j + 6 + 20 * p + 3 + 11 + 66 + 9 + 42 + 6)
     return float(total)
+
+
+def factor_stream_bytes_per_location(n, M):
+    """Bytes of candidate factor rows the screen reads for one location: every pool
+    candidate at step j reads its j float-float entries (8 bytes each)."""
+    return float(sum((M - (j + 1)) * j * 8 for j in range(n - 1)))
 
 
 def paper_form_flops_per_location(n0, n, M):
@@ -281,7 +287,9 @@ def roofline_for(prec, w, sel_ms, traffic):
             "traffic": traffic,
             "peak_source": "derived FP32: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane-cycle)",
             "work_per_location": work,
-            "work_unit": "FP32 operations of the float-float screen (add, mul or FMA = 1)"}
+            "work_unit": "FP32 operations of the float-float screen (add, mul or FMA = 1)",
+            "factor_stream_tbs": factor_stream_bytes_per_location(w.n, M) * T / (sel_ms / 1e3) / 1e12,
+            "factor_stream_note": "factor-row bytes read per second (shared memory + L2), kernels (b)+(c) time"}
 
 
 def stored_traffic(prec):
