@@ -93,6 +93,49 @@ def paper_form_flops_per_location(n0, n, M):
     return float(sum(2 * j * j * (M - j) for j in range(n0, n)))
 
 
+def mspe_flops_per_location(n0, n, M, p):
+    """Algorithmic FP64 flops of the MSPE design in the Cholesky basis for one location:
+    every pool candidate at step j costs 6j (three j-dots: u_c, its derivative row and the
+    Q-row product) + 3p + 1 + EXP_FLOPS (its correlation to the new point) + 40 (entries,
+    v, the derivative terms and J(c)); plus O(j^2) per step for the new rows of L^-1, Q, R."""
+    total = M * (3 * p + 1 + EXP_FLOPS)
+    for j in range(n - 1):
+        pool = M - (j + 1)
+        total += pool * (6 * j + 3 * p + 1 + EXP_FLOPS + 40) + 6 * j * j
+    return float(total)
+
+
+# The single-design workloads: generator, the (method, precision) variants timed, the
+# headline variant, the CPU-oracle sample size (about 10-30 s of work on 16 cores) and the
+# paper's own rate for the same problem where it gives one (BASELINE.md).
+def _workloads():
+    from paper_1303_0383_gb300 import inputs
+    return {
+        "paper-2d": dict(make=inputs.paper_2d, variants=[("alc", "fp64"), ("alc", "mixed")],
+                         head=("alc", "mixed"), cpu=1600, paper=None),
+        "smooth-8d": dict(make=inputs.smooth_8d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64")],
+                          head=("alc", "mixed"), cpu=120, paper=None),
+        "grid-2d": dict(make=inputs.grid_2d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("nn", "fp64")],
+                        head=("alc", "mixed"), cpu=1600,
+                        paper={"value": 10000 / 30.0, "what": "Sec. 4.1: about 30 s for 10K locations, "
+                               "40K-point 2-d design, ALC, n=50, fixed theta, 8 threads on a 4-core iMac"}),
+        "borehole": dict(make=lambda: inputs.borehole(4000, 500),
+                         variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("nn", "fp64")],
+                         head=("alc", "mixed"), cpu=500,
+                         paper={"value": 500 / 23.2, "what": "Table 1 alc.nomle: 23.2 s for 500 locations "
+                                "(fit + predict), N=4000, n=50, 8 threads on a 4-core iMac"}),
+        "borehole-8000": dict(make=lambda: inputs.borehole(8000, 1000),
+                              variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("nn", "fp64")],
+                              head=("alc", "mixed"), cpu=1000,
+                              paper={"value": 1000 / 45.1, "what": "Table SM.1 alc.nomle: 45.1 s for 1000 "
+                                     "locations (fit + predict), N=8000, n=50, 8 threads on a 4-core iMac"}),
+    }
+
+
+def vkey(method, prec):
+    return prec if method == "alc" else "%s_%s" % (method, prec)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -148,14 +191,14 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(r[3] for r in rows)}
 
 
-def cpu_oracle_sample(w, n_loc: int, seed: int = 0):
+def cpu_oracle_sample(w, n_loc: int, seed: int = 0, method: str = "alc"):
     """Times the CPU oracle (as it stands) on a seeded sample of the workload's locations."""
     import oracle
     oracle.build()
     locs = np.sort(np.random.default_rng(seed).choice(w.T, size=n_loc, replace=False))
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = oracle.predict(w.X, w.Z, w.XX[locs], w.n0, w.n, w.ncand, w.d, w.g, "alc", nthreads=cores)
+    r = oracle.predict(w.X, w.Z, w.XX[locs], w.n0, w.n, w.ncand, w.d, w.g, method, nthreads=cores)
     dt = time.perf_counter() - t0
     assert (r["status"] == 0).all()
     return n_loc / dt, cores, dt
@@ -220,12 +263,11 @@ def e2e_timing(args, w, M, method, prec, flush, idx_dev):
     return 1e3 * sum(times) / len(times)
 
 
-def time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch):
+def time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method="alc"):
     """Warm up, then time args.steps steps of kernel (a) + kernels (b)+(c) with CUDA events
     per kernel on the launching stream (L2 flushed between steps, outside the events)."""
     dev = X.device
     T, M = w.T, w.ncand
-    method = "alc"
     cand = torch.empty((T, M), dtype=torch.int32, device=dev)
     mean = torch.empty(T, dtype=torch.float64, device=dev)
     s2, var = torch.empty_like(mean), torch.empty_like(mean)
@@ -270,8 +312,18 @@ def barrier(torch):
     torch.cuda.synchronize()
 
 
-def roofline_for(prec, w, sel_ms, traffic):
+def roofline_for(prec, w, sel_ms, traffic, method="alc"):
     T, M = w.T, w.ncand
+    if method == "nn":
+        return None  # no scoring: kernels (b)+(c) only evaluate the predictive equations
+    if method == "mspe":
+        work = mspe_flops_per_location(w.n0, w.n, M, w.p)
+        achieved = work * T / (sel_ms / 1e3) / 1e12
+        return {"kernel": "select_mspe_kernel (kernels b+c)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "traffic": traffic,
+                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "work_per_location": work, "work_unit": "FP64 flops (FMA = 2, exp = 20)"}
     if prec == "fp64":
         work = select_flops_per_location(w.n0, w.n, M, w.p)
         achieved = work * T / (sel_ms / 1e3) / 1e12
@@ -313,14 +365,16 @@ def run_gpu(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", torch.cuda.current_device())
-    from paper_1303_0383_gb300 import inputs, lagp
+    from paper_1303_0383_gb300 import lagp
     lagp.load()
-    w = inputs.paper_2d()
+    spec = _workloads()[args.workload]
+    w = spec["make"]()
     if args.locations:
         w.XX = np.ascontiguousarray(w.XX[: args.locations])
         w.name += " (first %d locations)" % args.locations
-    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
-    head = "mixed" if "mixed" in precs else precs[0]
+    variants_run = [v for v in spec["variants"]
+                    if args.precision == "both" or v[1] == args.precision]
+    head = spec["head"] if spec["head"] in variants_run else variants_run[0]
     stream = torch.cuda.current_stream()
     X = torch.as_tensor(w.X).to(dev)
     Z = torch.as_tensor(w.Z).to(dev)
@@ -332,15 +386,15 @@ def run_gpu(args):
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
     sampler.start()
     res = {}
-    for prec in precs:
-        res[prec] = time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch)
+    for method, prec in variants_run:
+        k = vkey(method, prec)
+        res[k] = time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method=method)
         # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
-        res[prec]["e2e_ms"] = float("nan") if args.no_e2e else \
-            e2e_timing(args, w, w.ncand, "alc", prec, flush, res[prec]["idx"])
+        res[k]["e2e_ms"] = float("nan") if args.no_e2e else \
+            e2e_timing(args, w, w.ncand, method, prec, flush, res[k]["idx"])
     clocks = sampler.stop()
 
-    for prec in precs:
-        r = res[prec]
+    for k, r in res.items():
         if world > 1:
             import torch.distributed as dist
             tt = torch.tensor([r["ms"], r["e2e_ms"], r["sel_ms"]], dtype=torch.float64, device=dev)
@@ -355,44 +409,54 @@ def run_gpu(args):
     h2d = T * w.p * 8
     d2h = T * (8 * 3 + 4 * w.n + 1)
     variants = {}
-    for prec in precs:
-        r = res[prec]
-        variants[prec] = {
+    for method, prec in variants_run:
+        k = vkey(method, prec)
+        r = res[k]
+        variants[k] = {
+            "method": method, "precision": prec,
             "value": world * T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
             "kernels_ms": {"knn": r["knn_ms"], "select": r["sel_ms"]},
             "e2e": {"value": world * T / (r["e2e_ms"] / 1e3) if r["e2e_ms"] == r["e2e_ms"] else None,
                     "ms_per_step": r["e2e_ms"]},
             "gpu_launches": r["launches"],
-            "roofline": roofline_for(prec, w, r["sel_ms"], stored_traffic(prec)),
+            "roofline": roofline_for(prec, w, r["sel_ms"],
+                                     stored_traffic(prec) if (method == "alc" and args.workload == "paper-2d"
+                                                              and not args.locations) else None,
+                                     method=method),
         }
-    H = res[head]
+    hk = vkey(*head)
+    H = res[hk]
     cpu_val, cores, cpu_dt = (None, None, 0.0) if args.no_cpu else \
-        cpu_oracle_sample(w, min(args.cpu_sample, T))
+        cpu_oracle_sample(w, min(args.cpu_sample or spec["cpu"], T), method=head[0])
+    paper = spec["paper"]
     line = {
-        "metric": METRIC, "value": variants[head]["value"], "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": variants[hk]["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "f32x2+f64",
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (variants[hk]["value"] / paper["value"]) if paper else None,
+        "dtype": "f64" if head[1] == "fp64" else "f32x2+f64",
         "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "p": w.p, "T": w.T, "n0": w.n0, "n": w.n,
-                   "ncand": w.ncand, "d": w.d, "g": w.g, "method": "alc", "precision": head,
+                   "ncand": w.ncand, "d": w.d, "g": w.g, "method": head[0], "precision": head[1],
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas only: each GPU runs the whole workload"},
         "clocks": clocks,
-        "e2e": {"value": variants[head]["e2e"]["value"], "unit": UNIT,
+        "e2e": {"value": variants[hk]["e2e"]["value"], "unit": UNIT,
                 "ms_per_step": H["e2e_ms"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "lagp_predict (host buffers, pinned)"},
         "gpu_launches": H["launches"],
-        "kernels_ms": variants[head]["kernels_ms"],
-        "roofline": variants[head]["roofline"],
+        "kernels_ms": variants[hk]["kernels_ms"],
+        "roofline": variants[hk]["roofline"],
         "variants": variants,
         "paper_form_effective_tflops": {
-            prec: paper_form_flops_per_location(w.n0, w.n, w.ncand) * T / (res[prec]["sel_ms"] / 1e3) / 1e12
-            for prec in precs},
+            k: paper_form_flops_per_location(w.n0, w.n, w.ncand) * T / (res[k]["sel_ms"] / 1e3) / 1e12
+            for k in res if not k.startswith("nn")},
         "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d seeded locations of the %d (%.1f s wall)" %
-                                   (min(args.cpu_sample, T), w.T, cpu_dt)},
+                         "sample": "%d seeded locations of the %d, %s (%.1f s wall)" %
+                                   (min(args.cpu_sample or spec["cpu"], T), w.T, head[0], cpu_dt)},
     }
+    if paper:
+        line["paper_context"] = {"value": paper["value"], "unit": UNIT, "what": paper["what"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -542,13 +606,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
-    ap.add_argument("--cpu-sample", type=int, default=1600)
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="oracle sample size (0: the workload's default, about 10-30 s on 16 cores)")
     ap.add_argument("--ref-sample", type=int, default=160)
     ap.add_argument("--locations", type=int, default=0,
                     help="use only the first K locations (small case for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-API timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--workload", default="paper-2d", choices=["paper-2d", "batched", "serving"])
+    ap.add_argument("--workload", default="paper-2d",
+                    choices=["paper-2d", "smooth-8d", "grid-2d", "borehole", "borehole-8000", "batched",
+                             "serving"])
     ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--batch-T", type=int, default=20000)

@@ -4,9 +4,10 @@ This module only draws inputs; it holds none of the method's arithmetic (no
 correlation function, no design criterion, no predictive equation), so both the
 CUDA path and the CPU oracle can take their inputs from it.
 
-The workloads stand in for the paper's own test problems (Sec. 3.4: a 2-d surface
-on a dense 201x201 grid over [-2,2]^2; Sec. 5.2: the 8-d borehole function on an
-LHS), which are not shipped as data.  Shapes follow the five workload
+The first five workloads stand in for the paper's own test problems (Sec. 3.4: a 2-d
+surface on a dense 201x201 grid over [-2,2]^2; Sec. 5.2: the 8-d borehole function on
+an LHS), which are not shipped as data; grid_2d and borehole rebuild those two problems
+from their formulas.  Shapes follow the five workload
 descriptions below; every draw comes from numpy's PCG64 (``default_rng``) with
 seed 1303038300 + workload number, designs drawn first, then predictive sets,
 then noise.
@@ -98,6 +99,64 @@ def smooth_8d(T: int = 10000) -> Workload:
     Z = _surface_8d(X) + rng.normal(0.0, math.sqrt(1e-4), size=X.shape[0])
     return Workload("smooth-8d N=100000 T=%d n=100 M=2000" % T, X, Z, np.ascontiguousarray(XX),
                     n0=8, n=100, ncand=2000, d=1.0, g=1e-4)
+
+
+def _w_illustration(x: np.ndarray) -> np.ndarray:
+    # w(x) of the paper's illustration surface (Sec. 3.4)
+    return (np.exp(-(x - 1.0) ** 2) + np.exp(-0.8 * (x + 1.0) ** 2)
+            - 0.05 * np.sin(8.0 * (x + 0.1)))
+
+
+def grid_2d() -> Workload:
+    """The paper's illustration problem (Sec. 3.4): f(x1, x2) = -w(x1) w(x2) on the dense
+    201 x 201 regular grid over [-2, 2]^2 (40401 points), no noise.  Predictive set: 10000
+    locations (Sec. 4.1), placed on a 100 x 100 grid over [-1.97, 1.97]^2 (the paper does
+    not give their placement); every coordinate -1.97 + 3.94 k / 99 falls between design
+    grid lines, so distances to the design tie or nearly tie.  d = 0.5, g = 1e-6 as for the
+    other 2-d workloads; n0 = 6, n = 50, 1000 candidates (Sec. 3.4, Sec. 6)."""
+    X = _grid(-2.0, 2.0, 201)
+    Z = -_w_illustration(X[:, 0]) * _w_illustration(X[:, 1])
+    XX = _grid(-1.97, 1.97, 100)
+    return Workload("grid-2d N=40401 T=10000 n=50 M=1000", X, Z, XX,
+                    n0=6, n=50, ncand=1000, d=0.5, g=1e-6)
+
+
+# Ranges of the borehole function's eight inputs (Sec. 5.2), in the order
+# r_w, r, T_u, T_l, H_u, H_l, L, K_w.
+BOREHOLE_BOX = ((0.05, 0.15), (100.0, 5000.0), (63070.0, 115600.0), (63.1, 116.0),
+                (990.0, 1110.0), (700.0, 820.0), (1120.0, 1680.0), (9855.0, 12045.0))
+
+
+def borehole_response(U: np.ndarray) -> np.ndarray:
+    """Eq. borehole at coded inputs U in [0, 1]^8 (mapped linearly onto BOREHOLE_BOX)."""
+    lo = np.array([b[0] for b in BOREHOLE_BOX])
+    hi = np.array([b[1] for b in BOREHOLE_BOX])
+    V = lo + (hi - lo) * U
+    rw, r, Tu, Tl, Hu, Hl, L, Kw = (V[:, k] for k in range(8))
+    lg = np.log(r / rw)
+    return 2.0 * math.pi * Tu * (Hu - Hl) / (lg * (1.0 + 2.0 * L * Tu / (lg * rw ** 2 * Kw) + Tu / Tl))
+
+
+def latin_hypercube(rng: np.random.Generator, n: int, p: int) -> np.ndarray:
+    """Random Latin hypercube on [0, 1]^p: in every dimension each of the n strata
+    [i/n, (i+1)/n) holds exactly one point, at a uniform position inside it."""
+    strata = np.stack([rng.permutation(n) for _ in range(p)], axis=1)
+    return (strata + rng.random((n, p))) / n
+
+
+def borehole(N: int = 4000, Npred: int = 500) -> Workload:
+    """The borehole experiment (Sec. 5.2): one Latin hypercube of N + Npred points in the
+    coded 8-d box, the first N for the design and the rest for prediction; response by
+    Eq. borehole, no noise.  N = 4000 / Npred = 500 (Table 1) or 8000 / 1000 (Table SM.1).
+    d = 0.64, about the 10% quantile of squared distances between points of the coded
+    box (the paper's rule for the lengthscale's scale, Sec. 4.2; fixed here), g = 1e-6;
+    n0 = 6, n = 50, 1000 candidates."""
+    rng = np.random.default_rng(SEED_BASE + (6 if N <= 4000 else 7))
+    U = latin_hypercube(rng, N + Npred, 8)
+    X = np.ascontiguousarray(U[:N])
+    XX = np.ascontiguousarray(U[N:])
+    return Workload("borehole N=%d T=%d n=50 M=1000" % (N, Npred), X, borehole_response(X), XX,
+                    n0=6, n=50, ncand=1000, d=0.64, g=1e-6)
 
 
 def random_case(seed: int, N: int, p: int, T: int, n0: int, n: int, ncand: int,
