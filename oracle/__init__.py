@@ -75,6 +75,9 @@ def _lib(long_double: bool = False):
             L.orc_alc_forms.argtypes = [P, i32, i32, P, P, f64, f64, P]
             L.orc_corr.argtypes = [P, P, i32, f64]
             L.orc_corr.restype = f64
+            L.orc_mle.argtypes = [P, P, i64, i32, P, i32, f64, f64, f64, f64, i32, f64, P, P]
+            L.orc_mle_batch.argtypes = [P, P, i64, i32, i64, P, i32, P, f64, f64, f64, i32, f64,
+                                        P, P, P, i32]
             _libs[long_double] = L
         return _libs[long_double]
 
@@ -153,6 +156,37 @@ def design_predict(X, Z, x, idx, d: float, g: float, long_double: bool = False):
                                                 _p(idx), idx.shape[0], d, g, _p(out)),
            "design_predict")
     return float(out[0]), float(out[1]), float(out[2])
+
+
+NO_CONV = -9
+
+
+def mle(X, Z, idx, theta0: float, g: float, tmin: float, tmax: float, maxit: int = 100,
+        tol: float = 1e-8, long_double: bool = False):
+    """Local maximum-likelihood lengthscale of the design idx (Sec. 4.2 step 3; safeguarded
+    Newton on Eqs. dl, d2l); returns (theta, iterations, status)."""
+    X, Z, idx = _f64(X), _f64(Z), _i32(idx)
+    th, it = ctypes.c_double(), ctypes.c_int32()
+    st = _lib(long_double).orc_mle(_p(X), _p(Z), X.shape[0], X.shape[1], _p(idx), idx.shape[0],
+                                   theta0, g, tmin, tmax, maxit, tol, ctypes.byref(th),
+                                   ctypes.byref(it))
+    if st not in (OK, NOT_PD, NO_CONV):
+        _check(st, "mle")
+    return th.value, it.value, st
+
+
+def mle_batch(X, Z, idx, theta0, g: float, tmin: float, tmax: float, maxit: int = 100,
+              tol: float = 1e-8, nthreads: int = 0):
+    """orc_mle for every row of idx (T x n); theta0 scalar or length T.
+    Returns dict(theta, iters, status)."""
+    X, Z, idx = _f64(X), _f64(Z), _i32(idx)
+    T, n = idx.shape
+    th0 = _f64(np.broadcast_to(np.asarray(theta0, dtype=np.float64), (T,)))
+    th, it, st = np.empty(T), np.empty(T, np.int32), np.empty(T, np.int32)
+    _check(_lib().orc_mle_batch(_p(X), _p(Z), X.shape[0], X.shape[1], T, _p(idx), n, _p(th0), g,
+                                tmin, tmax, maxit, tol, _p(th), _p(it), _p(st), nthreads),
+           "mle_batch")
+    return {"theta": th, "iters": it, "status": st}
 
 
 def full_gp(X, Z, x, d: float, g: float):

@@ -16,7 +16,9 @@
  *   - the greedy local design D_{n0} -> D_n by ALC (Eq. dxy, read through SM "partial
  *     correlations", Eq. dxy2), by MSPE (Eq. mspe with Eqs. newv, G and the SM
  *     derivatives) or by nearest neighbours;
- *   - the Student-t predictive equations on D_n (Eqs. predgp, preds2).
+ *   - the Student-t predictive equations on D_n (Eqs. predgp, preds2);
+ *   - the local maximum-likelihood lengthscale of a design (Sec. 4.2, step 3) by
+ *     Newton's method on the analytic derivatives Eqs. dl, d2l (Sec. 3.2).
  * Every greedy step rebuilds K_j from its definition and refactors it from scratch
  * (hand-written Cholesky, K_j = L L^T); no quantity is carried from one step to the
  * next except the list of chosen points.  For ALC and for the predictive equations
@@ -69,6 +71,7 @@ typedef double real;
 #define LAGP_ORC_INVALID (-1)
 #define LAGP_ORC_OOM (-2)
 #define LAGP_ORC_NOT_PD (-5)
+#define LAGP_ORC_NO_CONV (-9)
 
 enum { ORC_ALC = 0, ORC_MSPE = 1, ORC_NN = 2, ORC_MSPE_NODERIV = 3 };
 
@@ -764,6 +767,85 @@ int orc_loglik(const double *Xd, const double *Y, int32_t j, int32_t p, double t
   free(K); free(L); free(Ki); free(Kd); free(Kdd); free(A); free(e); free(u); free(z); free(w);
   free(kdw); free(kikdw);
   return st;
+}
+
+/* Local maximum-likelihood lengthscale (Sec. 4.2, step 3): the theta in [tmin, tmax]
+ * maximising the log likelihood Eq. gpk of the design given by idx (n rows of X and Z),
+ * by Newton's method on l'(theta) = 0 with the analytic derivatives Eqs. dl, d2l
+ * (Sec. 3.2 names Newton-like methods; the safeguards are this oracle's reading):
+ *   - a bracket [a, b] is kept in which the maximum lies: l' > 0 at a (the likelihood
+ *     still increases there), l' < 0 at b; each iterate narrows it by the sign of l';
+ *   - the Newton step theta - l'/l'' is taken when l'' < 0 and it lands strictly inside
+ *     (a, b); otherwise the next iterate is the end of [tmin, tmax] uphill of theta (the
+ *     side l' points to) if that end has not been evaluated yet, else the bracket's
+ *     midpoint;
+ *   - it stops when a step is at most tol * theta (returning the new point), when l' = 0,
+ *     or at an end of [tmin, tmax] where l' points outward (the maximum on the boundary).
+ * *theta_out gets the estimate, *iters_out the number of derivative evaluations.
+ * Returns LAGP_ORC_OK, LAGP_ORC_NOT_PD (K_n not positive definite), LAGP_ORC_NO_CONV
+ * (maxit evaluations without meeting the stopping rule; the last iterate is returned)
+ * or LAGP_ORC_INVALID. */
+int orc_mle(const double *X, const double *Z, int64_t N, int32_t p, const int32_t *idx, int32_t n,
+            double theta0, double g, double tmin, double tmax, int32_t maxit, double tol,
+            double *theta_out, int32_t *iters_out) {
+  if (n < 2 || p < 1 || !(tmin > 0) || !(tmax > tmin) || maxit < 1 || !(tol > 0))
+    return LAGP_ORC_INVALID;
+  for (int a = 0; a < n; a++)
+    if (idx[a] < 0 || idx[a] >= N) return LAGP_ORC_INVALID;
+  double *Xd = malloc(sizeof(double) * (size_t)n * p), *Y = malloc(sizeof(double) * n);
+  if (!Xd || !Y) { free(Xd); free(Y); return LAGP_ORC_OOM; }
+  for (int a = 0; a < n; a++) {
+    for (int k = 0; k < p; k++) Xd[a * p + k] = X[(int64_t)idx[a] * p + k];
+    Y[a] = Z[idx[a]];
+  }
+  double lo = tmin, hi = tmax;
+  double th = theta0 < tmin ? tmin : (theta0 > tmax ? tmax : theta0);
+  int lo_open = 1, hi_open = 1;  /* the ends of [tmin, tmax] not yet evaluated */
+  int st = LAGP_ORC_NO_CONV, it = 0;
+  double l[3];
+  while (it < maxit) {
+    it++;
+    int e = orc_loglik(Xd, Y, n, p, th, g, l);
+    if (e) { st = e; break; }
+    const double d1 = l[1], d2 = l[2];
+    if (d1 == 0) { st = LAGP_ORC_OK; break; }
+    if (d1 > 0) {
+      lo = th; lo_open = 0;
+      if (th >= tmax) { st = LAGP_ORC_OK; break; }
+    } else {
+      hi = th; hi_open = 0;
+      if (th <= tmin) { st = LAGP_ORC_OK; break; }
+    }
+    double tn = (d2 < 0) ? th - d1 / d2 : NAN;
+    if (!(tn > lo && tn < hi)) {
+      if (d1 > 0 && hi_open) tn = hi;         /* uphill to an end not yet evaluated */
+      else if (d1 < 0 && lo_open) tn = lo;
+      else tn = 0.5 * (lo + hi);
+    }
+    const int done = fabs(tn - th) <= tol * th;
+    th = tn;
+    if (done) { st = LAGP_ORC_OK; break; }
+  }
+  *theta_out = th;
+  *iters_out = it;
+  free(Xd); free(Y);
+  return st;
+}
+
+/* orc_mle for T designs (idx: T x n), starting values theta0[t]; OpenMP over designs.
+ * status[t] is orc_mle's return value for design t. */
+int orc_mle_batch(const double *X, const double *Z, int64_t N, int32_t p, int64_t T,
+                  const int32_t *idx, int32_t n, const double *theta0, double g, double tmin,
+                  double tmax, int32_t maxit, double tol, double *theta_out, int32_t *iters_out,
+                  int32_t *status, int32_t nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < T; t++)
+    status[t] = orc_mle(X, Z, N, p, idx + t * n, n, theta0[t], g, tmin, tmax, maxit, tol,
+                        theta_out + t, iters_out + t);
+  return LAGP_ORC_OK;
 }
 
 /* Predictive quantities at a point xs given design (Xd, Y) of size j, and their theta

@@ -380,3 +380,60 @@ def test_long_double_oracle_agrees():
                                 forced=a["idx"], long_double=True)
         assert abs(a["mean"] - b["mean"]) <= 1e-8 * abs(b["mean"])
         assert abs(a["s2"] - b["s2"]) <= 1e-6 * b["s2"]
+
+
+# ---- local maximum-likelihood lengthscale (Sec. 4.2 step 3): pinned by the likelihood
+# itself (numpy slogdet/solve), not by the derivatives the Newton iteration uses
+
+def _mle_case(seed, n=30, p=2):
+    rng = np.random.default_rng(400 + seed)
+    X = rng.uniform(-1, 1, size=(n, p))
+    Z = np.sin(2.0 * X[:, 0]) + 0.3 * np.cos(3.0 * X[:, -1]) + 0.01 * rng.normal(size=n)
+    return X, Z, np.arange(n, dtype=np.int32)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mle_maximises_the_likelihood_on_a_grid(seed):
+    X, Z, idx = _mle_case(seed)
+    g = 1e-4
+    th, it, st = oracle.mle(X, Z, idx, 0.5, g, 1e-3, 20.0)
+    assert st == oracle.OK and 1 <= it < 100
+    grid = np.exp(np.linspace(np.log(1e-3), np.log(20.0), 2001))
+    ll = np.array([np_loglik(X, Z, t, g) for t in grid])
+    k = int(np.argmax(ll))
+    # the grid's best point brackets the estimate, and nothing on the grid beats it
+    assert grid[max(k - 1, 0)] <= th <= grid[min(k + 1, len(grid) - 1)]
+    assert np_loglik(X, Z, th, g) >= ll.max() - 1e-9 * abs(ll.max())
+    # an interior maximum: l' = 0 and l'' < 0 there
+    l, dl, d2l = oracle.loglik(X, Z, th, g)
+    assert abs(dl) <= 1e-6 * max(1.0, abs(d2l) * th) and d2l < 0
+
+
+def test_mle_from_different_starts_agrees():
+    X, Z, idx = _mle_case(5)
+    ths = [oracle.mle(X, Z, idx, t0, 1e-4, 1e-3, 20.0)[0] for t0 in (0.01, 0.3, 1.0, 15.0)]
+    assert max(ths) - min(ths) <= 1e-7 * max(ths), ths
+
+
+def test_mle_boundary_maximum():
+    X, Z, idx = _mle_case(1)
+    g = 1e-4
+    th_int = oracle.mle(X, Z, idx, 0.5, g, 1e-3, 20.0)[0]
+    # with the interval ending below the interior maximum the likelihood still rises at
+    # its upper end: the estimate is that end
+    th, it, st = oracle.mle(X, Z, idx, 0.5 * th_int, g, 1e-3, 0.6 * th_int)
+    assert st == oracle.OK and th == 0.6 * th_int
+    assert oracle.loglik(X, Z, th, g)[1] > 0
+    # and symmetrically at the lower end
+    th, it, st = oracle.mle(X, Z, idx, 3.0 * th_int, g, 2.0 * th_int, 20.0)
+    assert st == oracle.OK and th == 2.0 * th_int
+    assert oracle.loglik(X, Z, th, g)[1] < 0
+
+
+def test_mle_batch_matches_single():
+    X, Z, _ = _mle_case(2, n=60)
+    idx = np.stack([np.arange(i, i + 30) for i in (0, 10, 30)]).astype(np.int32)
+    b = oracle.mle_batch(X, Z, idx, [0.2, 0.5, 2.0], 1e-4, 1e-3, 20.0)
+    for t in range(3):
+        th, it, st = oracle.mle(X, Z, idx[t], [0.2, 0.5, 2.0][t], 1e-4, 1e-3, 20.0)
+        assert b["theta"][t] == th and b["iters"][t] == it and b["status"][t] == st
