@@ -61,6 +61,7 @@ extern "C" {
 #define LAGP_ERR_NO_DEVICE (-6)
 #define LAGP_ERR_UNSUPPORTED (-7)
 #define LAGP_ERR_SCRATCH_LIMIT (-8)
+#define LAGP_ERR_NO_CONVERGENCE (-9)
 
 typedef enum { LAGP_ALC = 0, LAGP_MSPE = 1, LAGP_NN = 2 } lagp_method;
 
@@ -257,6 +258,65 @@ int lagp_exp_dev(const double *x, double *y, int64_t n, void *stream);
  * points, all threads).  Used to report how many of the library's kernels a timed
  * region launched. */
 int64_t lagp_launch_count(void);
+
+/* ---- Local lengthscale estimates and the stagewise scheme (Sec. 4.2) ----
+ * Sec. 4.2: (1) start from a global theta_0; (2) build each location's design with
+ * theta_x; (3) estimate theta_x by maximum likelihood on that design; (4) set theta_x to
+ * the estimate and repeat (2)-(3) as desired; predict on the last design with the last
+ * estimate.  lagp_select_dev performs (2) with theta_0, lagp_mle_dev (3),
+ * lagp_select_theta_dev (2) with per-location theta_x, lagp_design_predict_dev the output.
+ * No spatial smoothing of the estimates is applied (the paper's borehole runs used the
+ * unsmoothed first-stage estimates). */
+
+/* Kernels (b)+(c) with a lengthscale per location: lagp_select_dev, except that location
+ * t uses theta[t] (device array of T values, each > 0; the caller guarantees this) for
+ * its candidate scores and predictive equations.  The workspace is sized by
+ * lagp_select_workspace_bytes. */
+int lagp_select_theta_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                          const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                          int32_t n0, int32_t n, const double *theta, double g, int32_t method,
+                          int32_t precision, double *mean, double *s2, double *var, int32_t *idx,
+                          int8_t *status, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Scratch bytes lagp_mle_dev needs for T designs of size n. */
+size_t lagp_mle_workspace_bytes(int64_t T, int32_t n);
+
+/* Local maximum-likelihood lengthscale, step (3): for each location t, the theta in
+ * [tmin, tmax] maximising the log likelihood of Eq. gpk for the design
+ * idx[t*n .. t*n+n) (design rows of X and Z), by Newton's method on the analytic
+ * derivatives Eqs. dl, d2l (Sec. 3.2), started from theta0_loc[t] (device, T values) or,
+ * when theta0_loc is NULL, from theta0.  Safeguards: a bracket of the maximum is narrowed
+ * by the sign of l'; the Newton step is taken when l'' < 0 and it stays inside the
+ * bracket, otherwise the iterate goes to the end of [tmin, tmax] uphill of theta if that
+ * end has not been evaluated, else to the bracket's midpoint; the iteration stops when a
+ * step is at most tol * theta (the new point is returned), when l' = 0, or at an end of
+ * [tmin, tmax] where l' points outward (a boundary maximum).  All arithmetic is FP64.
+ * Arguments: N >= 1, p in [1, 8], T >= 0, 2 <= n <= 256, 0 < tmin < tmax, maxit >= 1,
+ * tol > 0, g >= 0; idx device, T x n (a row whose first entry is negative, a location
+ * whose screen failed, gives NaN and LAGP_ERR_NOT_PD).
+ * Outputs (device): theta_out[T]; iters[T] (int32, optional): derivative evaluations;
+ * status[T] (int8, optional): 0, LAGP_ERR_NOT_PD (K_n not positive definite in FP64) or
+ * LAGP_ERR_NO_CONVERGENCE (maxit evaluations; theta_out holds the last iterate). */
+int lagp_mle_dev(const double *X, const double *Z, int64_t N, int32_t p, int64_t T,
+                 const int32_t *idx, int32_t n, double theta0, const double *theta0_loc,
+                 double g, double tmin, double tmax, int32_t maxit, double tol,
+                 double *theta_out, int32_t *iters, int8_t *status, void *workspace,
+                 size_t workspace_bytes, void *stream);
+
+/* Scratch bytes lagp_design_predict_dev needs. */
+size_t lagp_design_predict_workspace_bytes(int64_t T, int32_t n);
+
+/* Kernel (c) alone, the output step: the predictive equations (Eqs. predgp, preds2) at
+ * XX[t] on the given design idx[t*n .. t*n+n) with lengthscale theta_loc[t] (device) or,
+ * when theta_loc is NULL, theta; FP64.  Argument rules as lagp_select_dev (n >= 3,
+ * theta > 0 is checked for the scalar only).  A row of idx whose first entry is negative
+ * gives NaN outputs and status LAGP_ERR_NOT_PD, as does a K_n that is not positive
+ * definite.  Outputs (device): mean[T], s2[T] required; var[T], status[T] optional. */
+int lagp_design_predict_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                            const double *XX, int64_t T, const int32_t *idx, int32_t n,
+                            double theta, const double *theta_loc, double g, double *mean,
+                            double *s2, double *var, int8_t *status, void *workspace,
+                            size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -92,6 +92,7 @@ const char *lagp_strerror(int code) {
     case LAGP_ERR_NO_DEVICE: return "no usable CUDA device";
     case LAGP_ERR_UNSUPPORTED: return "method/precision combination not supported by this build";
     case LAGP_ERR_SCRATCH_LIMIT: return "problem too large for the static scratch of the no-allocation entry point";
+    case LAGP_ERR_NO_CONVERGENCE: return "iteration limit reached before the stopping rule was met";
     default: return "unknown error code";
   }
 }
@@ -171,7 +172,7 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
   if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
-  a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g;
+  a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
@@ -274,4 +275,75 @@ int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, 
   return cuda_status(es);
 }
 
+// ---- stagewise scheme (Sec. 4.2) ----
+
+int lagp_select_theta_dev(const double *X, const double *Z, int64_t N, int32_t p, const double *XX,
+                          int64_t T, const int32_t *cand, int32_t ncand, int32_t n0, int32_t n,
+                          const double *theta, double g, int32_t method, int32_t precision,
+                          double *mean, double *s2, double *var, int32_t *idx, int8_t *status,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+  int st = check_common(N, p, T, n0, n, ncand, 1.0, g, method, precision);
+  if (st) return st;
+  st = check_supported(method, precision);
+  if (st) return st;
+  if (T > 0 && (!X || !Z || !XX || !cand || !theta || !mean || !s2 || !workspace))
+    return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  SelectArgs a;
+  a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
+  a.M = ncand; a.n0 = n0; a.n = n; a.theta = 1.0; a.g = g; a.theta_loc = theta;
+  a.method = method; a.precision = precision;
+  a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
+  return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+size_t lagp_mle_workspace_bytes(int64_t T, int32_t n) {
+  DevInfo di;
+  if (dev_info(&di) || T < 0 || n < 2 || n > kMaxN) return 0;
+  return mle_workspace_bytes(T, n, di.num_sms);
+}
+
+int lagp_mle_dev(const double *X, const double *Z, int64_t N, int32_t p, int64_t T,
+                 const int32_t *idx, int32_t n, double theta0, const double *theta0_loc,
+                 double g, double tmin, double tmax, int32_t maxit, double tol,
+                 double *theta_out, int32_t *iters, int8_t *status, void *workspace,
+                 size_t workspace_bytes, void *stream) {
+  if (N < 1 || p < 1 || p > kMaxP || T < 0 || n < 2 || n > kMaxN || !(tmin > 0) ||
+      !(tmax > tmin) || maxit < 1 || !(tol > 0) || !(g >= 0) || !(theta0 > 0))
+    return LAGP_ERR_INVALID_ARG;
+  if (T == 0) return LAGP_OK;
+  if (!X || !Z || !idx || !theta_out || !workspace) return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  MleArgs a;
+  a.X = X; a.Z = Z; a.p = p; a.T = T; a.idx = idx; a.n = n; a.theta0 = theta0;
+  a.theta0_loc = theta0_loc; a.g = g; a.tmin = tmin; a.tmax = tmax; a.tol = tol; a.maxit = maxit;
+  a.theta_out = theta_out; a.iters = iters; a.status = status;
+  return mle_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+size_t lagp_design_predict_workspace_bytes(int64_t T, int32_t n) {
+  DevInfo di;
+  if (dev_info(&di) || T < 0 || n < 3 || n > kMaxN) return 0;
+  return predict_fp64_workspace_bytes(T, n, di.num_sms);
+}
+
+int lagp_design_predict_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                            const double *XX, int64_t T, const int32_t *idx, int32_t n,
+                            double theta, const double *theta_loc, double g, double *mean,
+                            double *s2, double *var, int8_t *status, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+  if (N < 1 || p < 1 || p > kMaxP || T < 0 || n < 3 || n > kMaxN || n > N || !(theta > 0) ||
+      !(g >= 0))
+    return LAGP_ERR_INVALID_ARG;
+  if (T == 0) return LAGP_OK;
+  if (!X || !Z || !XX || !idx || !mean || !s2 || !workspace) return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  PredictArgs a;
+  a.X = X; a.Z = Z; a.p = p; a.XX = XX; a.T = T; a.n = n; a.nmax = n; a.theta = theta; a.g = g;
+  a.idx = idx; a.B = BatchView{nullptr, nullptr, nullptr, 0, theta_loc};
+  a.mean = mean; a.s2 = s2; a.var = var; a.status = status;
+  return predict_fp64_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"
+

@@ -30,6 +30,7 @@ struct BatchView {
   const LocDesc *locs;         // T descriptors
   const int32_t *order;        // queue position -> location (cost-sorted), may be nullptr
   int ldxx;                    // row stride of XX in doubles
+  const double *theta_loc;     // per-location lengthscale (T), or nullptr
 };
 
 // A location's parameters, resolved from the tables or the uniform values.
@@ -63,6 +64,10 @@ __device__ __forceinline__ LocParams resolve_loc(const BatchView &B, int64_t q, 
     L.x = XX + q * p;
     L.cand = cand + q * M;
     L.idx = idx ? idx + q * n : nullptr;
+  }
+  if (B.theta_loc) {  // a lengthscale per location (stage 2 of the stagewise scheme)
+    L.theta = B.theta_loc[L.loc];
+    L.theta_inv = 1.0 / L.theta;
   }
   return L;
 }

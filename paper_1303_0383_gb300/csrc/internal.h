@@ -49,6 +49,7 @@ struct SelectArgs {
   const int32_t *cand;
   int32_t M, n0, n;
   double theta, g;
+  const double *theta_loc;  // per-location lengthscale (device, T), or nullptr: theta
   int32_t method, precision;
   double *mean, *s2, *var;
   int32_t *idx;
@@ -84,6 +85,25 @@ struct PredictArgs {
 size_t predict_fp64_workspace_bytes(int64_t T, int32_t nmax, int num_sms);
 int predict_fp64_launch(const PredictArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
 int predict_fp64_prepare();
+
+// Local maximum-likelihood lengthscale of each location's design (mle.cu).
+struct MleArgs {
+  const double *X, *Z;
+  int32_t p;
+  int64_t T;
+  const int32_t *idx;
+  int32_t n;
+  double theta0;
+  const double *theta0_loc;
+  double g, tmin, tmax, tol;
+  int32_t maxit;
+  double *theta_out;
+  int32_t *iters;
+  int8_t *status;
+};
+size_t mle_workspace_bytes(int64_t T, int32_t n, int num_sms);
+int mle_launch(const MleArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+int mle_prepare();
 
 // MSPE variant of kernels (b)+(c), FP64.
 size_t select_mspe_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);

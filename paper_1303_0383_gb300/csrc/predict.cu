@@ -11,19 +11,14 @@
 // v_n(x) = 1 + g - |u_x|^2 is a cancellation whose rounding error is of the order of the
 // tolerance, and keeping the textbook operation order keeps this kernel's rounding close
 // to that of a plain sequential evaluation.
-// FP64 runs at 1/64 of the FP32 rate on this GPU, so every FP64 instruction is kept busy
-// on all lanes: the matrix entries and each step's trailing update are flattened over
-// the threads; a division by the pivot is a product with its reciprocal plus one
-// correction (Markstein: with the correctly rounded reciprocal y of b and q = rn(a y),
-// q + (a - b q) y gives the correctly rounded a / b), and the pivot's square root and
-// reciprocal are taken by the thread that finishes the pivot, so a step costs two block
-// barriers.
+// The factorisation is fp64_chol.cuh's, flattened over the CTA's threads.
 //
 // One CTA owns one location at a time (persistent CTAs over a work queue); the matrix
 // lives in shared memory when it fits, else in a per-CTA slot of the workspace.
 #include <math.h>
 
 #include "batch.cuh"
+#include "fp64_chol.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -57,14 +52,6 @@ __device__ __forceinline__ double corr(const double *a, const double *b, int p, 
     acc = fma(t, t, acc);
   }
   return exp_nonpos(-acc * theta_inv, etab);
-}
-
-// Row t of the lower triangle {(a, b): 0 <= b <= a} holding flat entry e.
-__device__ __forceinline__ int tri_row(int e) {
-  int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  while (a * (a + 1) / 2 > e) a--;
-  while ((a + 1) * (a + 2) / 2 <= e) a++;
-  return a;
 }
 
 __global__ void __launch_bounds__(PB) predict_fp64_kernel(PredParams P) {
@@ -106,46 +93,7 @@ __global__ void __launch_bounds__(PB) predict_fp64_kernel(PredParams P) {
                                           : L.Z[d[a]];
         }
       }
-      __syncthreads();
-      if (tid == 0) {
-        const double d0 = A[0];
-        if (!(d0 > 0.0)) sh_fail = 1;
-        const double l0 = sqrt(d0);
-        A[0] = l0;
-        rl[0] = 1.0 / l0;
-      }
-      __syncthreads();
-      for (int k = 0; k < n && !sh_fail; k++) {
-        const double lkk = A[k * lda + k], r = rl[k];
-        // column k and the extra columns of row k divided by the pivot
-        for (int i = k + 1 + tid; i < n + 2; i += PB) {
-          double *ap = (i < n) ? &A[i * lda + k] : &A[k * lda + i];
-          const double a = *ap, q = a * r;
-          *ap = fma(fma(-q, lkk, a), r, q);
-        }
-        __syncthreads();
-        // a_il -= l_ik l_lk for k < l <= i, and the extra columns: b_i -= l_ik b_k
-        const int rows = n - k - 1, ntr = rows * (rows + 1) / 2;
-        for (int e = tid; e < ntr + 2 * rows; e += PB) {
-          if (e < ntr) {
-            const int t = tri_row(e), c = e - t * (t + 1) / 2;
-            const int i = k + 1 + t, l = k + 1 + c;
-            const double v = fma(-A[i * lda + k], A[l * lda + k], A[i * lda + l]);
-            if (e == 0) {  // the next pivot is final: its square root and reciprocal
-              if (!(v > 0.0)) sh_fail = 1;
-              const double lv = sqrt(v);
-              A[i * lda + l] = lv;
-              rl[k + 1] = 1.0 / lv;
-            } else {
-              A[i * lda + l] = v;
-            }
-          } else {
-            const int i = k + 1 + ((e - ntr) >> 1), col = (e - ntr) & 1;
-            A[i * lda + n + col] = fma(-A[i * lda + k], A[k * lda + n + col], A[i * lda + n + col]);
-          }
-        }
-        __syncthreads();
-      }
+      chol_flat_fp64(A, n, lda, 2, rl, &sh_fail);
     }
     __syncthreads();
     if (tid == 0) {

@@ -272,7 +272,7 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   P.g = a.g;
   P.nmax = a.n;
   P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -316,7 +316,7 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   P.g = a.g;
   P.nmax = a.n;
   P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -372,7 +372,7 @@ int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStr
   P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
   P.M = b.Mmax; P.Mpad = Mpad; P.n0 = 0; P.n = b.nmax; P.method = b.method;
   P.theta = 1.0; P.g = 0.0; P.nmax = b.nmax; P.pmax = b.pmax;
-  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx};
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
   P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);

@@ -333,7 +333,7 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   P.M = a.M; P.Mpad = mix_mpad(a.M); P.Qpad = P.Mpad / 2; P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
   PredictArgs pa;
   pa.X = a.X; pa.Z = a.Z; pa.p = a.p; pa.XX = a.XX; pa.T = a.T; pa.n = a.n; pa.nmax = a.n;
   pa.theta = a.theta; pa.g = a.g; pa.idx = nullptr; pa.B = P.B;
@@ -361,7 +361,7 @@ int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, i
   P.M = b.Mmax; P.Mpad = mix_mpad(b.Mmax); P.Qpad = P.Mpad / 2; P.n0 = 0; P.n = b.nmax;
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;
-  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx};
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
   PredictArgs pa;
   pa.X = nullptr; pa.Z = nullptr; pa.p = b.pmax; pa.XX = b.XX; pa.T = b.T; pa.n = b.nmax;
   pa.nmax = b.nmax; pa.theta = 1.0; pa.g = 0.0; pa.idx = nullptr; pa.B = P.B;

@@ -82,6 +82,16 @@ def load(path: str | None = None):
                                          ctypes.c_uint32, P, sz, P]
     L.lagp_select_dev_noalloc.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
                                           i32, i32, P, P, P, P, P, P]
+    L.lagp_select_theta_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, P, f64, i32,
+                                        i32, P, P, P, P, P, P, sz, P]
+    L.lagp_mle_workspace_bytes.argtypes = [i64, i32]
+    L.lagp_mle_workspace_bytes.restype = sz
+    L.lagp_mle_dev.argtypes = [P, P, i64, i32, i64, P, i32, f64, P, f64, f64, f64, i32, f64, P, P,
+                               P, P, sz, P]
+    L.lagp_design_predict_workspace_bytes.argtypes = [i64, i32]
+    L.lagp_design_predict_workspace_bytes.restype = sz
+    L.lagp_design_predict_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, f64, P, f64, P, P, P, P,
+                                          P, sz, P]
     _lib = L
     return L
 
@@ -353,3 +363,95 @@ def predict_torch(X, Z, XX, n0, n, ncand, theta, g, method="alc", precision="fp6
     lagp_predict_dev(X, Z, XX, n0, n, ncand, theta, g, method, precision, mean, s2, var, idx,
                      status, ws)
     return dict(mean=mean, s2=s2, var=var, idx=idx, status=status)
+
+
+# ------------------------------------------------ stagewise scheme (Sec. 4.2), device API
+
+def lagp_select_theta_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2, var=None,
+                          idx=None, status=None, ws=None, stream=None) -> None:
+    """Kernels (b)+(c) with a lengthscale per location: theta is a (T,) float64 tensor."""
+    N, p = X.shape
+    T, M = cand.shape
+    _chk(load().lagp_select_theta_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(cand), M, n0, n,
+                                      _dp(theta), g, _m(method), _pr(precision), _dp(mean),
+                                      _dp(s2), _dp(var), _dp(idx), _dp(status), _dp(ws),
+                                      ws.numel(), _stream(stream)), "lagp_select_theta_dev")
+
+
+def lagp_mle_workspace_bytes(T: int, n: int) -> int:
+    return int(load().lagp_mle_workspace_bytes(T, n))
+
+
+def lagp_mle_dev(X, Z, idx, theta0, g, tmin, tmax, theta_out, iters=None, status=None,
+                 maxit: int = 100, tol: float = 1e-8, ws=None, stream=None) -> None:
+    """Local maximum-likelihood lengthscale of each design (idx (T,n) int32); theta0 a float
+    or a (T,) float64 tensor of starting values."""
+    N, p = X.shape
+    T, n = idx.shape
+    th_loc = theta0 if not isinstance(theta0, (int, float)) else None
+    th_s = float(theta0) if th_loc is None else 1.0
+    _chk(load().lagp_mle_dev(_dp(X), _dp(Z), N, p, T, _dp(idx), n, th_s, _dp(th_loc), g, tmin,
+                             tmax, maxit, tol, _dp(theta_out), _dp(iters), _dp(status), _dp(ws),
+                             ws.numel(), _stream(stream)), "lagp_mle_dev")
+
+
+def lagp_design_predict_workspace_bytes(T: int, n: int) -> int:
+    return int(load().lagp_design_predict_workspace_bytes(T, n))
+
+
+def lagp_design_predict_dev(X, Z, XX, idx, theta, g, mean, s2, var=None, status=None, ws=None,
+                            stream=None) -> None:
+    """Kernel (c) on given designs idx (T,n); theta a float or a (T,) float64 tensor."""
+    N, p = X.shape
+    T, n = idx.shape
+    th_loc = theta if not isinstance(theta, (int, float)) else None
+    th_s = float(theta) if th_loc is None else 1.0
+    _chk(load().lagp_design_predict_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(idx), n, th_s,
+                                        _dp(th_loc), g, _dp(mean), _dp(s2), _dp(var), _dp(status),
+                                        _dp(ws), ws.numel(), _stream(stream)),
+         "lagp_design_predict_dev")
+
+
+def predict_stagewise(X, Z, XX, n0, n, ncand, theta0, g, method="alc", precision="fp64",
+                      stages: int = 2, tmin=None, tmax=None, maxit: int = 100, tol: float = 1e-8,
+                      stream=None):
+    """The stagewise scheme of Sec. 4.2 on device tensors, every step in the library's
+    kernels: candidates (kernel (a)); design with theta0 (kernels (b)+(c)); local MLE;
+    then stages - 1 times: design with the per-location estimates and a fresh MLE; finally
+    the predictive equations on the last design with the last estimates.  stages = 1 gives
+    the one-stage scheme with local MLE ("alc"/"mspe" rows); stages = 2 the two-stage
+    ("alc2"/"mspe2").  tmin/tmax default to theta0/100 and 100 theta0.
+    Returns dict(mean, s2, var, idx, theta, iters, status)."""
+    import torch
+    dev = X.device
+    N, p = X.shape
+    T = XX.shape[0]
+    tmin = theta0 / 100.0 if tmin is None else tmin
+    tmax = theta0 * 100.0 if tmax is None else tmax
+    f64, i32 = torch.float64, torch.int32
+    cand = torch.empty((T, ncand), dtype=i32, device=dev)
+    lagp_knn_dev(X, XX, ncand, cand, workspace(lagp_knn_workspace_bytes(N, T, ncand), dev), stream)
+    mean = torch.empty(T, dtype=f64, device=dev)
+    s2, var = torch.empty_like(mean), torch.empty_like(mean)
+    idx = torch.empty((T, n), dtype=i32, device=dev)
+    status = torch.empty(T, dtype=torch.int8, device=dev)
+    mstatus = torch.empty(T, dtype=torch.int8, device=dev)
+    theta = torch.empty(T, dtype=f64, device=dev)
+    iters = torch.empty(T, dtype=i32, device=dev)
+    ws_sel = workspace(lagp_select_workspace_bytes(T, p, n, ncand, method, precision), dev)
+    ws_mle = workspace(lagp_mle_workspace_bytes(T, n), dev)
+    lagp_select_dev(X, Z, XX, cand, n0, n, theta0, g, method, precision, mean, s2, var, idx,
+                    status, ws_sel, stream)
+    lagp_mle_dev(X, Z, idx, theta0, g, tmin, tmax, theta, iters, mstatus, maxit, tol, ws_mle,
+                 stream)
+    for _ in range(stages - 1):
+        # a location without an estimate (its screen failed) keeps theta0
+        th1 = torch.where(torch.isfinite(theta), theta, torch.full_like(theta, theta0))
+        lagp_select_theta_dev(X, Z, XX, cand, n0, n, th1, g, method, precision, mean, s2, var,
+                              idx, status, ws_sel, stream)
+        lagp_mle_dev(X, Z, idx, th1, g, tmin, tmax, theta, iters, mstatus, maxit, tol, ws_mle,
+                     stream)
+    ws_pr = workspace(lagp_design_predict_workspace_bytes(T, n), dev)
+    lagp_design_predict_dev(X, Z, XX, idx, theta, g, mean, s2, var, status, ws_pr, stream)
+    return dict(mean=mean, s2=s2, var=var, idx=idx, theta=theta, iters=iters, status=status,
+                mle_status=mstatus)

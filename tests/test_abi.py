@@ -111,3 +111,37 @@ def test_server_arguments_are_checked_on_the_host():
                                     a["ncand"], a["max_batch"], a["budget"], a["max_slots"],
                                     C.byref(out)) == lagp.LAGP_ERR_INVALID_ARG, b
     assert L.lagp_server_destroy(None) == lagp.LAGP_ERR_INVALID_ARG
+
+
+def test_mle_and_stagewise_entry_points_reject_bad_arguments():
+    L = lagp.load()
+    P = ctypes.c_void_p
+    dummy = ctypes.c_double(0.0)
+    d = ctypes.cast(ctypes.pointer(dummy), P)
+    bad = [
+        # N, p, T, n, theta0, g, tmin, tmax, maxit, tol
+        (0, 2, 1, 10, 0.5, 0.0, 0.01, 1.0, 10, 1e-8),
+        (100, 9, 1, 10, 0.5, 0.0, 0.01, 1.0, 10, 1e-8),
+        (100, 2, 1, 1, 0.5, 0.0, 0.01, 1.0, 10, 1e-8),
+        (100, 2, 1, 10, 0.5, 0.0, 0.0, 1.0, 10, 1e-8),
+        (100, 2, 1, 10, 0.5, 0.0, 1.0, 1.0, 10, 1e-8),
+        (100, 2, 1, 10, 0.5, 0.0, 0.01, 1.0, 0, 1e-8),
+        (100, 2, 1, 10, 0.5, 0.0, 0.01, 1.0, 10, 0.0),
+        (100, 2, 1, 10, -1.0, 0.0, 0.01, 1.0, 10, 1e-8),
+        (100, 2, 1, 10, 0.5, -1.0, 0.01, 1.0, 10, 1e-8),
+    ]
+    for N, p, T, n, th0, g, tmin, tmax, maxit, tol in bad:
+        assert L.lagp_mle_dev(d, d, N, p, T, d, n, th0, None, g, tmin, tmax, maxit, tol, d, None,
+                              None, d, 1 << 20, None) == lagp.LAGP_ERR_INVALID_ARG
+    # T = 0 is a no-op even without buffers
+    assert L.lagp_mle_dev(None, None, 100, 2, 0, None, 10, 0.5, None, 0.0, 0.01, 1.0, 10, 1e-8,
+                          None, None, None, None, 0, None) == lagp.LAGP_OK
+    # kernel (c) alone: n >= 3, theta > 0
+    assert L.lagp_design_predict_dev(d, d, 100, 2, d, 1, d, 2, 0.5, None, 0.0, d, d, None, None, d,
+                                     1 << 20, None) == lagp.LAGP_ERR_INVALID_ARG
+    assert L.lagp_design_predict_dev(d, d, 100, 2, d, 1, d, 10, 0.0, None, 0.0, d, d, None, None,
+                                     d, 1 << 20, None) == lagp.LAGP_ERR_INVALID_ARG
+    # per-location theta select: the theta array is required
+    assert L.lagp_select_theta_dev(d, d, 100, 2, d, 1, d, 20, 6, 10, None, 0.0, 0, 0, d, d, None,
+                                   None, None, d, 1 << 20, None) == lagp.LAGP_ERR_INVALID_ARG
+    assert lagp.strerror(-9).startswith("iteration limit")
