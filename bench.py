@@ -303,7 +303,8 @@ def time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method="
     sel_ms = [e[1].elapsed_time(e[2]) for e in evs]
     step_ms = [a + b for a, b in zip(knn_ms, sel_ms)]
     return dict(ms=sum(step_ms) / len(step_ms), knn_ms=sum(knn_ms) / len(knn_ms),
-                sel_ms=sum(sel_ms) / len(sel_ms), launches=int(launches), idx=idx)
+                sel_ms=sum(sel_ms) / len(sel_ms), launches=int(launches), idx=idx,
+                mean=mean.cpu().numpy(), s2=s2.cpu().numpy())
 
 
 def barrier(torch):
@@ -357,6 +358,127 @@ def stored_traffic(prec):
     return None
 
 
+def time_stagewise(args, w, method, prec, stages, X, Z, XX, flush, stream, lagp, torch):
+    """The stagewise scheme of Sec. 4.2 (lagp.predict_stagewise's calls, with CUDA events
+    between them): candidates, design at theta0, local MLE, stages-1 times (design at the
+    estimates, MLE), predictive equations on the last design.  Returns timings, the
+    outputs of the last step and the mean Newton iterations."""
+    dev = X.device
+    T, M, n, N, p = w.T, w.ncand, w.n, w.N, w.p
+    tmin, tmax = w.d / 100.0, w.d * 100.0
+    f64, i32 = torch.float64, torch.int32
+    cand = torch.empty((T, M), dtype=i32, device=dev)
+    mean = torch.empty(T, dtype=f64, device=dev)
+    s2, var = torch.empty_like(mean), torch.empty_like(mean)
+    idx = torch.empty((T, n), dtype=i32, device=dev)
+    status = torch.empty(T, dtype=torch.int8, device=dev)
+    mst = torch.empty(T, dtype=torch.int8, device=dev)
+    theta = torch.empty(T, dtype=f64, device=dev)
+    th1 = torch.empty_like(theta)
+    iters = torch.empty(T, dtype=i32, device=dev)
+    ws_knn = lagp.workspace(lagp.lagp_knn_workspace_bytes(N, T, M), dev)
+    ws_sel = lagp.workspace(lagp.lagp_select_workspace_bytes(T, p, n, M, method, prec), dev)
+    ws_mle = lagp.workspace(lagp.lagp_mle_workspace_bytes(T, n), dev)
+    ws_pr = lagp.workspace(lagp.lagp_design_predict_workspace_bytes(T, n), dev)
+    it_sum = [0]
+
+    def step(evs=None):
+        marks = []
+        rec = (lambda: marks.append(torch.cuda.Event(enable_timing=True)) or marks[-1].record(stream)) \
+            if evs is not None else (lambda: None)
+        rec()
+        lagp.lagp_knn_dev(X, XX, M, cand, ws_knn, stream)
+        rec()
+        lagp.lagp_select_dev(X, Z, XX, cand, w.n0, n, w.d, w.g, method, prec, mean, s2, var, idx,
+                             status, ws_sel, stream)
+        rec()
+        lagp.lagp_mle_dev(X, Z, idx, w.d, w.g, tmin, tmax, theta, iters, mst, 100, 1e-8, ws_mle,
+                          stream)
+        rec()
+        for _ in range(stages - 1):
+            th1.copy_(theta)
+            lagp.lagp_select_theta_dev(X, Z, XX, cand, w.n0, n, th1, w.g, method, prec, mean, s2,
+                                       var, idx, status, ws_sel, stream)
+            rec()
+            lagp.lagp_mle_dev(X, Z, idx, th1, w.g, tmin, tmax, theta, iters, mst, 100, 1e-8,
+                              ws_mle, stream)
+            rec()
+        lagp.lagp_design_predict_dev(X, Z, XX, idx, theta, w.g, mean, s2, var, status, ws_pr,
+                                     stream)
+        rec()
+        if evs is not None:
+            evs.append(marks)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert int((status != 0).sum()) == 0 and int((mst != 0).sum()) == 0, "failed locations"
+    launches0 = lagp.lagp_launch_count()
+    evs = []
+    barrier(torch)
+    for k in range(args.steps):
+        flush.add_(1.0)
+        step(evs)
+    barrier(torch)
+    launches = lagp.lagp_launch_count() - launches0
+    names = ["knn", "select", "mle"]
+    for k in range(2, stages + 1):
+        names += ["select_theta_%d" % k, "mle_%d" % k]
+    names.append("predict")
+    kern = {nm: sum(m[i].elapsed_time(m[i + 1]) for m in evs) / len(evs) for i, nm in enumerate(names)}
+    ms = sum(kern.values())
+    return dict(ms=ms, kernels_ms=kern, launches=int(launches), idx=idx,
+                mean=mean.cpu().numpy(), s2=s2.cpu().numpy(),
+                newton_iters=float(iters.double().mean()))
+
+
+def accuracy(w, mean, s2):
+    """Out-of-sample accuracy against the known response at XX (the paper's Sec. 5 metrics):
+    RMSE, sqrt(1 - NSE) = sd(error) / sd(response), and the coverage of the 95% Student-t
+    interval with n degrees of freedom."""
+    if w.ZZ is None:
+        return None
+    from scipy import stats
+    err = mean - w.ZZ
+    q = stats.t.ppf(0.975, w.n)
+    cover = float(np.mean(np.abs(err) <= q * np.sqrt(s2)))
+    return {"rmse": float(np.sqrt(np.mean(err ** 2))),
+            "sqrt_1_minus_nse": float(np.std(err) / np.std(w.ZZ)), "coverage95": cover}
+
+
+# The paper's rates for its stagewise rows (with local MLE), where it states the
+# predictive-set size: Table 1 (borehole N=4000, 500 locations) and Table SM.1 (N=8000,
+# 1000 locations), seconds for fit + predict on 8 threads of a 4-core iMac.
+PAPER_STAGEWISE = {("borehole", 1): 500 / 23.5, ("borehole", 2): 500 / 46.3,
+                   ("borehole-8000", 1): 1000 / 46.2, ("borehole-8000", 2): 1000 / 92.3}
+
+
+def print_stagewise(args, w, spec, variants, clocks, world):
+    head = spec["head"]
+    hk = vkey(head[0] + (str(args.stages) if args.stages > 1 else "") + "_mle", head[1])
+    if hk not in variants:
+        hk = next(iter(variants))
+    paper = PAPER_STAGEWISE.get((args.workload, args.stages))
+    line = {
+        "metric": "local-GP predictions/sec, stagewise scheme with local MLE (Sec. 4.2), %d stage(s)"
+                  % args.stages,
+        "value": variants[hk]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": variants[hk]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": variants[hk]["value"] / paper if paper else None,
+        "dtype": "f64" if head[1] == "fp64" else "f32x2+f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "p": w.p, "T": w.T, "n0": w.n0, "n": w.n,
+                   "ncand": w.ncand, "theta0": w.d, "g": w.g, "tmin": w.d / 100, "tmax": w.d * 100,
+                   "stages": args.stages, "l2": "flushed between timed steps (256 MB write)"},
+        "clocks": clocks, "gpu_launches": variants[hk]["gpu_launches"], "variants": variants,
+    }
+    if paper:
+        line["paper_context"] = {"value": paper, "unit": UNIT,
+                                 "what": "the paper's %s row (fit + predict, 8 threads, 4-core iMac)"
+                                         % (head[0] + ("2" if args.stages == 2 else ""))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
     rank, world, local = env_rank()
@@ -371,6 +493,8 @@ def run_gpu(args):
     w = spec["make"]()
     if args.locations:
         w.XX = np.ascontiguousarray(w.XX[: args.locations])
+        if w.ZZ is not None:
+            w.ZZ = w.ZZ[: args.locations]
         w.name += " (first %d locations)" % args.locations
     variants_run = [v for v in spec["variants"]
                     if args.precision == "both" or v[1] == args.precision]
@@ -388,6 +512,16 @@ def run_gpu(args):
     res = {}
     for method, prec in variants_run:
         k = vkey(method, prec)
+        if args.stages:
+            # the stagewise scheme with local MLE: the paper's alc/mspe (1 stage) and
+            # alc2/mspe2 (2 stages) rows; device buffers only (no host API for it)
+            k = vkey(method + (str(args.stages) if args.stages > 1 else "") + "_mle", prec)
+            r = time_stagewise(args, w, method, prec, args.stages, X, Z, XX, flush, stream, lagp,
+                               torch)
+            r.update(knn_ms=r["kernels_ms"]["knn"], sel_ms=r["ms"] - r["kernels_ms"]["knn"],
+                     e2e_ms=float("nan"))
+            res[k] = r
+            continue
         res[k] = time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method=method)
         # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
         res[k]["e2e_ms"] = float("nan") if args.no_e2e else \
@@ -409,7 +543,14 @@ def run_gpu(args):
     h2d = T * w.p * 8
     d2h = T * (8 * 3 + 4 * w.n + 1)
     variants = {}
-    for method, prec in variants_run:
+    for k, r in res.items():
+        if args.stages:
+            variants[k] = {"value": world * T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
+                           "kernels_ms": r["kernels_ms"], "gpu_launches": r["launches"],
+                           "newton_iters_mean": r["newton_iters"],
+                           "accuracy": accuracy(w, r["mean"], r["s2"])}
+            continue
+    for method, prec in ([] if args.stages else variants_run):
         k = vkey(method, prec)
         r = res[k]
         variants[k] = {
@@ -423,7 +564,10 @@ def run_gpu(args):
                                      stored_traffic(prec) if (method == "alc" and args.workload == "paper-2d"
                                                               and not args.locations) else None,
                                      method=method),
+            "accuracy": accuracy(w, r["mean"], r["s2"]),
         }
+    if args.stages:
+        return print_stagewise(args, w, spec, variants, clocks, world)
     hk = vkey(*head)
     H = res[hk]
     cpu_val, cores, cpu_dt = (None, None, 0.0) if args.no_cpu else \
@@ -619,6 +763,8 @@ def main():
     ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--batch-T", type=int, default=20000)
+    ap.add_argument("--stages", type=int, default=0,
+                    help="time the stagewise scheme with local MLE (Sec. 4.2): 1 or 2 stages")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

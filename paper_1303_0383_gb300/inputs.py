@@ -36,6 +36,7 @@ class Workload:
     ncand: int
     d: float      # lengthscale theta of exp(-||x-x'||^2 / theta)
     g: float      # nugget eta
+    ZZ: np.ndarray | None = None  # the noise-free response at XX, where it is known
 
     @property
     def N(self) -> int:
@@ -117,8 +118,9 @@ def grid_2d() -> Workload:
     X = _grid(-2.0, 2.0, 201)
     Z = -_w_illustration(X[:, 0]) * _w_illustration(X[:, 1])
     XX = _grid(-1.97, 1.97, 100)
+    ZZ = -_w_illustration(XX[:, 0]) * _w_illustration(XX[:, 1])
     return Workload("grid-2d N=40401 T=10000 n=50 M=1000", X, Z, XX,
-                    n0=6, n=50, ncand=1000, d=0.5, g=1e-6)
+                    n0=6, n=50, ncand=1000, d=0.5, g=1e-6, ZZ=ZZ)
 
 
 # Ranges of the borehole function's eight inputs (Sec. 5.2), in the order
@@ -156,7 +158,7 @@ def borehole(N: int = 4000, Npred: int = 500) -> Workload:
     X = np.ascontiguousarray(U[:N])
     XX = np.ascontiguousarray(U[N:])
     return Workload("borehole N=%d T=%d n=50 M=1000" % (N, Npred), X, borehole_response(X), XX,
-                    n0=6, n=50, ncand=1000, d=0.64, g=1e-6)
+                    n0=6, n=50, ncand=1000, d=0.64, g=1e-6, ZZ=borehole_response(XX))
 
 
 def random_case(seed: int, N: int, p: int, T: int, n0: int, n: int, ncand: int,
