@@ -259,6 +259,25 @@ int lagp_exp_dev(const double *x, double *y, int64_t n, void *stream);
  * region launched. */
 int64_t lagp_launch_count(void);
 
+/* Design augmentation (Sec. 6: with the indices of the local designs saved, "designs can
+ * be augmented, picking up where they left off"): kernels (b)+(c) where location t's
+ * design starts from the n1 saved points start[t*n1 .. t*n1+n1) (design indices in
+ * selection order, e.g. a previous call's idx) instead of its n0 nearest neighbours, and
+ * grows greedily to n points.  The greedy choice depends only on the current design, so
+ * augmenting the first n1 points of a design of size n reproduces that design.  Every
+ * saved point must be among the location's ncand candidates (the same X, x and ncand as
+ * the call that chose it); a location where one is not gets NaN outputs and status
+ * LAGP_ERR_NOT_PD.  method ALC or MSPE (n1 >= 3 for MSPE); NN returns
+ * LAGP_ERR_UNSUPPORTED (its design does not depend on the start).  Rules otherwise as
+ * lagp_select_dev with n0 := n1 (1 <= n1 <= n); the workspace is sized by
+ * lagp_select_workspace_bytes. */
+int lagp_select_augment_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                            const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                            const int32_t *start, int32_t n1, int32_t n, double theta, double g,
+                            int32_t method, int32_t precision, double *mean, double *s2,
+                            double *var, int32_t *idx, int8_t *status, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
 /* ---- Local lengthscale estimates and the stagewise scheme (Sec. 4.2) ----
  * Sec. 4.2: (1) start from a global theta_0; (2) build each location's design with
  * theta_x; (3) estimate theta_x by maximum likelihood on that design; (4) set theta_x to

@@ -61,6 +61,8 @@ def _lib(long_double: bool = False):
             L.orc_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
             L.orc_local_design.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64, i32,
                                            P, P, P, P, P, P]
+            L.orc_local_design_start.argtypes = [P, P, i64, i32, P, P, i32, P, i32, i32, f64, f64,
+                                                 i32, P, P, P, P, P, P]
             L.orc_predict.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32,
                                       P, P, P, P, P, P, i32]
             L.orc_full_gp.argtypes = [P, P, i64, i32, P, f64, f64, P, P]
@@ -112,10 +114,15 @@ def knn(X, XX, M: int, nthreads: int = 0, with_d2: bool = False):
 
 
 def local_design(X, Z, x, cand, n0: int, n: int, d: float, g: float, method="alc",
-                 forced=None, long_double: bool = False):
+                 forced=None, long_double: bool = False, start=None):
     """Greedy local design and predictive equations at one location (Sec. 3; Eqs.
-    dxy, mspe, predgp, preds2).  Returns dict(idx, mean, s2, var, trace)."""
+    dxy, mspe, predgp, preds2).  With start (n0 design indices) the design grows from
+    that saved design instead of the n0 nearest (Sec. 6).  Returns dict(idx, mean, s2,
+    var, trace)."""
     X, Z, x, cand = _f64(X), _f64(Z), _f64(x), _i32(cand)
+    if start is not None:
+        sz = _i32(start)
+        n0 = sz.shape[0]
     N, p = X.shape
     M = cand.shape[0]
     m = METHODS.get(method, method) if isinstance(method, str) else int(method)
@@ -123,10 +130,16 @@ def local_design(X, Z, x, cand, n0: int, n: int, d: float, g: float, method="alc
     out = np.empty(3, np.float64)
     trace = np.full((max(n - n0, 1), TRACE_W), np.nan)
     fz = _i32(forced) if forced is not None else None
-    st = _lib(long_double).orc_local_design(
-        _p(X), _p(Z), N, p, _p(x), _p(cand), M, n0, n, d, g, m,
-        _p(fz) if fz is not None else None, _p(idx), _p(out[0:]), _p(out[1:]), _p(out[2:]),
-        _p(trace))
+    if start is not None:
+        st = _lib(long_double).orc_local_design_start(
+            _p(X), _p(Z), N, p, _p(x), _p(cand), M, _p(sz), n0, n, d, g, m,
+            _p(fz) if fz is not None else None, _p(idx), _p(out[0:]), _p(out[1:]), _p(out[2:]),
+            _p(trace))
+    else:
+        st = _lib(long_double).orc_local_design(
+            _p(X), _p(Z), N, p, _p(x), _p(cand), M, n0, n, d, g, m,
+            _p(fz) if fz is not None else None, _p(idx), _p(out[0:]), _p(out[1:]), _p(out[2:]),
+            _p(trace))
     return dict(status=st, idx=idx, mean=out[0], s2=out[1], var=out[2], trace=trace[: n - n0])
 
 

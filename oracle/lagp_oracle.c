@@ -429,15 +429,23 @@ static int mspe_prepare(const prob_t *P, work_t *W, const int32_t *cand, const d
  * cand: the M nearest (rank order).  forced: n design indices or NULL.
  * idx_out: n design indices.  trace: (n-n0) x TRACE_W or NULL. */
 static int local_design(const prob_t *P, work_t *W, const double *x, const int32_t *cand,
-                        int n0, int n, int method, const int32_t *forced, int32_t *idx_out,
-                        double *mean, double *s2, double *var, double *trace) {
+                        int n0, int n, int method, const int32_t *forced, const int32_t *start,
+                        int32_t *idx_out, double *mean, double *s2, double *var, double *trace) {
   int M = W->M;
   real onepg = 1 + P->g;
   memset(W->used, 0, (size_t)M);
   for (int c = 0; c < M; c++) W->kx[c] = corr_r(x, cand_pt(P, cand, c), P->p, P->theta);
+  /* the start design: the n0 nearest, or the saved design start[0..n0) (Sec. 6) */
   for (int i = 0; i < n0; i++) {
-    W->dr[i] = i;
-    W->used[i] = 1;
+    int r = i;
+    if (start) {
+      r = -1;
+      for (int c = 0; c < M; c++)
+        if (cand[c] == start[i]) { r = c; break; }
+      if (r < 0 || W->used[r]) return LAGP_ORC_INVALID;
+    }
+    W->dr[i] = r;
+    W->used[r] = 1;
     fill_Kc_row(P, W, cand, i);
   }
   for (int j = n0; j < n; j++) {
@@ -589,7 +597,26 @@ int orc_local_design(const double *X, const double *Z, int64_t N, int32_t p, con
   prob_t P = {X, Z, N, p, (real)theta, (real)g};
   work_t W;
   if (work_alloc(&W, n, M)) return LAGP_ORC_OOM;
-  st = local_design(&P, &W, x, cand, n0, n, method, forced, idx, mean, s2, var, trace);
+  st = local_design(&P, &W, x, cand, n0, n, method, forced, NULL, idx, mean, s2, var, trace);
+  work_free(&W);
+  return st;
+}
+
+/* orc_local_design grown from a saved start design (Sec. 6, "picking up where they left
+ * off"): the first n1 members are start[0..n1) (design indices, each one of the location's
+ * candidates), then greedy steps to n.  LAGP_ORC_INVALID if a start index is not a
+ * candidate or repeats. */
+int orc_local_design_start(const double *X, const double *Z, int64_t N, int32_t p,
+                           const double *x, const int32_t *cand, int32_t M, const int32_t *start,
+                           int32_t n1, int32_t n, double theta, double g, int32_t method,
+                           const int32_t *forced, int32_t *idx, double *mean, double *s2,
+                           double *var, double *trace) {
+  int st = check_args(N, p, 1, n1, n, M, theta, g, method);
+  if (st) return st;
+  prob_t P = {X, Z, N, p, (real)theta, (real)g};
+  work_t W;
+  if (work_alloc(&W, n, M)) return LAGP_ORC_OOM;
+  st = local_design(&P, &W, x, cand, n1, n, method, forced, start, idx, mean, s2, var, trace);
   work_free(&W);
   return st;
 }
@@ -621,7 +648,7 @@ int orc_predict(const double *X, const double *Z, int64_t N, int32_t p, const do
 #pragma omp for schedule(dynamic, 1)
     for (int64_t t = 0; t < T; t++) {
       if (!ok) continue;
-      int s = local_design(&P, &W, XX + t * p, cand + t * M, n0, n, method, NULL,
+      int s = local_design(&P, &W, XX + t * p, cand + t * M, n0, n, method, NULL, NULL,
                            idx + t * n, mean + t, s2 + t, var + t, NULL);
       status[t] = s;
       if (s) { mean[t] = NAN; s2[t] = NAN; var[t] = NAN; }

@@ -173,6 +173,7 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
   a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
+  a.start = nullptr; a.nstart = 0;
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
@@ -277,6 +278,29 @@ int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, 
 
 // ---- stagewise scheme (Sec. 4.2) ----
 
+int lagp_select_augment_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                            const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                            const int32_t *start, int32_t n1, int32_t n, double theta, double g,
+                            int32_t method, int32_t precision, double *mean, double *s2,
+                            double *var, int32_t *idx, int8_t *status, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+  int st = check_common(N, p, T, n1, n, ncand, theta, g, method, precision);
+  if (st) return st;
+  st = check_supported(method, precision);
+  if (st) return st;
+  if (method == LAGP_NN) return LAGP_ERR_UNSUPPORTED;
+  if (T > 0 && (!X || !Z || !XX || !cand || !start || !mean || !s2 || !workspace))
+    return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  SelectArgs a;
+  a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
+  a.M = ncand; a.n0 = n1; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
+  a.start = start; a.nstart = n1;
+  a.method = method; a.precision = precision;
+  a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
+  return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
 int lagp_select_theta_dev(const double *X, const double *Z, int64_t N, int32_t p, const double *XX,
                           int64_t T, const int32_t *cand, int32_t ncand, int32_t n0, int32_t n,
                           const double *theta, double g, int32_t method, int32_t precision,
@@ -292,6 +316,7 @@ int lagp_select_theta_dev(const double *X, const double *Z, int64_t N, int32_t p
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
   a.M = ncand; a.n0 = n0; a.n = n; a.theta = 1.0; a.g = g; a.theta_loc = theta;
+  a.start = nullptr; a.nstart = 0;
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));

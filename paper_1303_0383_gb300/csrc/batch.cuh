@@ -72,4 +72,19 @@ __device__ __forceinline__ LocParams resolve_loc(const BatchView &B, int64_t q, 
   return L;
 }
 
+// A saved start design (design augmentation): sr[i] = the rank of start[i] in the
+// location's candidate list cnd (M entries), or -1 when it is not a candidate.  Block-
+// cooperative; every thread returns after the same two barriers.
+__device__ __forceinline__ void start_ranks(const int32_t *start, int nstart, const int32_t *cnd,
+                                            int M, int *sr) {
+  for (int i = threadIdx.x; i < nstart; i += blockDim.x) sr[i] = -1;
+  __syncthreads();
+  for (int c = threadIdx.x; c < M; c += blockDim.x) {
+    const int32_t v = cnd[c];
+    for (int i = 0; i < nstart; i++)
+      if (start[i] == v) sr[i] = c;
+  }
+  __syncthreads();
+}
+
 }  // namespace lagp

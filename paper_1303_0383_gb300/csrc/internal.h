@@ -50,6 +50,8 @@ struct SelectArgs {
   int32_t M, n0, n;
   double theta, g;
   const double *theta_loc;  // per-location lengthscale (device, T), or nullptr: theta
+  const int32_t *start;     // saved start designs (device, T x nstart), or nullptr: n0 nearest
+  int32_t nstart;
   int32_t method, precision;
   double *mean, *s2, *var;
   int32_t *idx;

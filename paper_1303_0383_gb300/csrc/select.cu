@@ -56,6 +56,8 @@ struct SelParams {
   double *Xc;     // gridDim.x slots of pmax x Mpad
   int *queue;
   BatchView B;    // per-location tables (B.designs == nullptr: uniform launch)
+  const int32_t *start;  // saved start designs (T x nstart design indices), or nullptr
+  int nstart;
 };
 
 // ALC scores are compared as fractions cov^2 / v without dividing: a/da beats b/db when
@@ -75,6 +77,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
   double *ux = srow + nmax;             // nmax  (u_x = L^{-1} k(x))
   double *yt = ux + nmax;               // nmax  (ytil = L^{-1} Y)
   unsigned char *used = reinterpret_cast<unsigned char *>(yt + nmax);  // Mpad
+  int *sr = reinterpret_cast<int *>(used + Mpad);                     // nmax: start ranks
   __shared__ double xs[kMaxP], xl[kMaxP];
   __shared__ double red_s[SB / 32], red_d[SB / 32];
   __shared__ int red_r[SB / 32];
@@ -100,9 +103,12 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
     if (tid < p) xl[tid] = L.x[tid];
     if (tid == 0) { sh_fail = 0; sh_vx = L.onepg; sh_psi = 0.0; }
     __syncthreads();
+    // the start design: the n0 nearest, or a saved design (augmentation)
+    const int n0e = P.start ? P.nstart : L.n0;
+    if (P.start) start_ranks(P.start + loc * P.nstart, P.nstart, cnd, M, sr);
     // Stage candidate coordinates; v = K(c,c) = 1+g, cov_0(x,c) = K(x,c).
     // NN, and ALC without greedy steps (n0 == n), never look past rank n-1
-    const int limit = (P.method == LAGP_NN || L.n0 == n) ? n : M;
+    const int limit = ((P.method == LAGP_NN || n0e == n) && !P.start) ? n : M;
     for (int c = tid; c < limit; c += SB) {
       const double *xc = L.X + (int64_t)cnd[c] * p;
       double acc = 0.0;
@@ -120,8 +126,8 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
 
     int s = 0;
     for (int j = 0; j < n; j++) {
-      if (j >= L.n0 && P.method == LAGP_ALC) s = sh_best;
-      else s = j;
+      if (j >= n0e && P.method == LAGP_ALC) s = sh_best;
+      else s = (P.start && j < n0e) ? sr[j] : j;
       if (s < 0) {  // nothing admissible left
         if (tid == 0) sh_fail = 1;
         __syncthreads();
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
       if (sh_fail) break;
       if (j == n - 1) break;
       const double inv = sh_inv, uxj = sh_uxj;
-      const bool want_score = (P.method == LAGP_ALC) && (j + 1 >= L.n0);
+      const bool want_score = (P.method == LAGP_ALC) && (j + 1 >= n0e);
       double bs = -1.0, bd = 1.0;   // best score as a fraction bs/bd (none yet: -1)
       int br = 0x7fffffff;
       for (int c = tid; c < limit; c += SB) {
@@ -234,7 +240,8 @@ int sel_grid(int64_t T, int num_sms) {
 int mpad_of(int M) { return (int)align_up((size_t)M, 32); }
 
 size_t sel_smem_bytes(int Mpad, int n) {
-  return (size_t)(2 * Mpad + 3 * n) * sizeof(double) + align_up((size_t)Mpad, 16);
+  return (size_t)(2 * Mpad + 3 * n) * sizeof(double) + align_up((size_t)Mpad, 16) +
+         align_up((size_t)n * sizeof(int), 16);
 }
 
 }  // namespace
@@ -273,6 +280,7 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   P.nmax = a.n;
   P.pmax = a.p;
   P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.start = a.start; P.nstart = a.nstart;
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -317,6 +325,7 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   P.nmax = a.n;
   P.pmax = a.p;
   P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.start = a.start; P.nstart = a.nstart;
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -373,6 +382,7 @@ int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStr
   P.M = b.Mmax; P.Mpad = Mpad; P.n0 = 0; P.n = b.nmax; P.method = b.method;
   P.theta = 1.0; P.g = 0.0; P.nmax = b.nmax; P.pmax = b.pmax;
   P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
+  P.start = nullptr; P.nstart = 0;
   P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);

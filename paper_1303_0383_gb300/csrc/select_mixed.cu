@@ -50,6 +50,8 @@ struct MixParams {
   double *A;     // slots of n x (n + 2): FP64 factorisation
   int *queue;
   int *rescores; // count of FP64 re-score passes (diagnostics)
+  const int32_t *start;  // saved start designs (T x nstart design indices), or nullptr
+  int nstart;
 };
 
 #ifndef LAGP_MIX_MINB
@@ -103,8 +105,10 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     const int32_t *cnd = L.cand;
     const ff onepg = ff_from_double(L.onepg);
     const ff thinv = ff_from_double(L.theta_inv);
+    // the start design: the n0 nearest, or a saved design (augmentation)
+    const int n0e = P.start ? P.nstart : L.n0;
     // Without greedy steps (n0 == n) only the start design's own rows are ever read.
-    const int Q = ((L.n0 == n ? n : M) + 1) >> 1;
+    const int Q = ((n0e == n && !P.start ? n : M) + 1) >> 1;
     if (tid < p) xl[tid] = L.x[tid];
     if (tid == 0) sh_fail = 0;
     __syncthreads();
@@ -139,10 +143,11 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       cp[q] = make_float4(cv[0].h, cv[1].h, cv[0].l, cv[1].l);
     }
     __syncthreads();
+    if (P.start) start_ranks(P.start + L.loc * P.nstart, P.nstart, cnd, M, dr);
 
     int best = 0;
     for (int j = 0; j < n; j++) {
-      const int s = (j < L.n0) ? j : best;
+      const int s = (j < n0e) ? (P.start ? dr[j] : j) : best;
       if (s < 0) {  // nothing admissible left (the same for every thread)
         if (tid == 0) sh_fail = 1;
         break;
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       }
       __syncwarp();
       if (j == n - 1) break;
-      const bool want = j + 1 >= L.n0;
+      const bool want = j + 1 >= n0e;
       const ff2 inv2{f2s(inv.h), f2s(inv.l)}, uxj2{f2s(uxj.h), f2s(uxj.l)};
       const ff2 thinv2{f2s(thinv.h), f2s(thinv.l)};
       float b1 = -1.0f, b2 = -1.0f;
@@ -334,6 +339,7 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
   P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.start = a.start; P.nstart = a.nstart;
   PredictArgs pa;
   pa.X = a.X; pa.Z = a.Z; pa.p = a.p; pa.XX = a.XX; pa.T = a.T; pa.n = a.n; pa.nmax = a.n;
   pa.theta = a.theta; pa.g = a.g; pa.idx = nullptr; pa.B = P.B;
@@ -362,6 +368,7 @@ int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, i
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;
   P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
+  P.start = nullptr; P.nstart = 0;
   PredictArgs pa;
   pa.X = nullptr; pa.Z = nullptr; pa.p = b.pmax; pa.XX = b.XX; pa.T = b.T; pa.n = b.nmax;
   pa.nmax = b.nmax; pa.theta = 1.0; pa.g = 0.0; pa.idx = nullptr; pa.B = P.B;

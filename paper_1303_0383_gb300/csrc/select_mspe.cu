@@ -47,6 +47,8 @@ struct MspeParams {
   double *cs;         // slots of 4 x Mpad: kdz, pd, q, m per candidate
   double *Li, *Kd, *Kdd, *Q;  // slots of n x n
   int *queue;
+  const int32_t *start;  // saved start designs (T x nstart design indices), or nullptr
+  int nstart;
 };
 
 __device__ __forceinline__ bool j_better(double a, int ra, double b, int rb) {
@@ -107,7 +109,9 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
       sh_psi = 0.0; sh_vx = L.onepg; sh_trR = 0.0; sh_nQ2 = 0.0; sh_yRy = 0.0;
     }
     __syncthreads();
-    const int limit = (L.n0 == n) ? n : M;
+    // the start design: the n0 nearest, or a saved design (augmentation)
+    const int n0e = P.start ? P.nstart : L.n0;
+    const int limit = (n0e == n && !P.start) ? n : M;
     for (int c = tid; c < limit; c += TB) {
       const double *xc = L.X + (int64_t)cnd[c] * p;
       double acc = 0.0;
@@ -123,9 +127,10 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
       used[c] = 0;
     }
     __syncthreads();
+    if (P.start) start_ranks(P.start + L.loc * P.nstart, P.nstart, cnd, M, dr);
 
     for (int j = 0; j < n; j++) {
-      const int s = (j < L.n0) ? j : sh_best;
+      const int s = (j < n0e) ? (P.start ? dr[j] : j) : sh_best;
       if (s < 0) {
         if (tid == 0) sh_fail = 1;
         __syncthreads();
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
       const double uxj = sh_d[1], rj = sh_d[3], F = sh_d[4], dmux = sh_d[5], wKdw = sh_d[6];
       const double psi = sh_psi, vx = sh_vx, qjj = qrow[j];
       const int jn = j + 1;  // design size after this step
-      const bool want = (jn >= L.n0) && (jn >= 3);
+      const bool want = (jn >= n0e) && (jn >= 3);
       const double dj = (double)(jn - 2);
       double bs = INFINITY;
       int br = 0x7fffffff;
@@ -382,10 +387,11 @@ int mspe_grid(int64_t T, int num_sms) {
 }
 
 struct MspeLayout {
-  size_t u, ud, xc, cs, nn, total;
+  size_t u, ud, xc, cs, nn, idx, pred, total;
 };
 
-MspeLayout mspe_layout(int G, int p, int n, int M) {
+// [queue | U | Ud | Xc | cs | Li, Kd, Kdd, Q | design indices | kernel (c) workspace]
+MspeLayout mspe_layout(int G, int p, int n, int M, int64_t T, int64_t idx_total, int num_sms) {
   const size_t Mpad = align_up((size_t)M, 32);
   MspeLayout L;
   L.u = align_up((size_t)G * n * Mpad * sizeof(double), 256);
@@ -393,7 +399,9 @@ MspeLayout mspe_layout(int G, int p, int n, int M) {
   L.xc = align_up((size_t)G * p * Mpad * sizeof(double), 256);
   L.cs = align_up((size_t)G * 4 * Mpad * sizeof(double), 256);
   L.nn = align_up((size_t)G * n * n * sizeof(double), 256);
-  L.total = 256 + L.u + L.ud + L.xc + L.cs + 4 * L.nn;
+  L.idx = align_up((size_t)idx_total * sizeof(int32_t), 256);
+  L.pred = predict_fp64_workspace_bytes(T, n, num_sms);
+  L.total = 256 + L.u + L.ud + L.xc + L.cs + 4 * L.nn + L.idx + L.pred;
   return L;
 }
 
@@ -402,10 +410,46 @@ size_t mspe_smem_bytes(int Mpad, int n) {
          align_up((size_t)Mpad, 16);
 }
 
+// The design kernel, then kernel (c) (predict.cu) on the designs it selected: the
+// predictive equations are re-evaluated from a fresh FP64 factorisation in the textbook
+// operation order, which tracks a sequential evaluation more closely in the strongly
+// cancelling cases than the step-by-step updates do.
+int mspe_run(MspeParams P, const MspeLayout &L, int G, char *w, int32_t *user_idx,
+             const DevInfo &di, cudaStream_t stream) {
+  P.queue = reinterpret_cast<int *>(w);
+  size_t off = 256;
+  P.U = reinterpret_cast<double *>(w + off); off += L.u;
+  P.Ud = reinterpret_cast<double *>(w + off); off += L.ud;
+  P.Xc = reinterpret_cast<double *>(w + off); off += L.xc;
+  P.cs = reinterpret_cast<double *>(w + off); off += L.cs;
+  P.Li = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.Kd = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.Kdd = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.Q = reinterpret_cast<double *>(w + off); off += L.nn;
+  P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(w + off);
+  off += L.idx;
+  const size_t smem = mspe_smem_bytes(P.Mpad, P.nmax);
+  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
+  cudaError_t e = cudaFuncSetAttribute(select_mspe_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  select_mspe_kernel<<<G, TB, smem, stream>>>(P);
+  g_launches.fetch_add(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  PredictArgs pa;
+  pa.X = P.X; pa.Z = P.Z; pa.p = P.pmax; pa.XX = P.XX; pa.T = P.T; pa.n = P.n; pa.nmax = P.nmax;
+  pa.theta = P.theta; pa.g = P.g; pa.idx = P.idx; pa.B = P.B;
+  pa.mean = P.mean; pa.s2 = P.s2; pa.var = P.var; pa.status = P.status;
+  return predict_fp64_launch(pa, w + off, L.pred, stream);
+}
+
 }  // namespace
 
 size_t select_mspe_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms) {
-  return mspe_layout(mspe_grid(T, num_sms), p, n, ncand).total;
+  return mspe_layout(mspe_grid(T, num_sms), p, n, ncand, T, T * n, num_sms).total;
 }
 
 int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
@@ -416,40 +460,23 @@ int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStrea
   st = exp_table_upload();
   if (st) return st;
   const int G = mspe_grid(a.T, di.num_sms);
-  const MspeLayout L = mspe_layout(G, a.p, a.n, a.M);
+  const MspeLayout L = mspe_layout(G, a.p, a.n, a.M, a.T, a.T * a.n, di.num_sms);
   if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
-  char *w = static_cast<char *>(ws);
   MspeParams P;
   P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = (int)align_up((size_t)a.M, 32); P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
   P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
-  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
-  P.queue = reinterpret_cast<int *>(w);
-  size_t off = 256;
-  P.U = reinterpret_cast<double *>(w + off); off += L.u;
-  P.Ud = reinterpret_cast<double *>(w + off); off += L.ud;
-  P.Xc = reinterpret_cast<double *>(w + off); off += L.xc;
-  P.cs = reinterpret_cast<double *>(w + off); off += L.cs;
-  P.Li = reinterpret_cast<double *>(w + off); off += L.nn;
-  P.Kd = reinterpret_cast<double *>(w + off); off += L.nn;
-  P.Kdd = reinterpret_cast<double *>(w + off); off += L.nn;
-  P.Q = reinterpret_cast<double *>(w + off); off += L.nn;
-  const size_t smem = mspe_smem_bytes(P.Mpad, a.n);
-  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(select_mspe_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
-  if (e != cudaSuccess) return cuda_status(e);
-  select_mspe_kernel<<<G, TB, smem, stream>>>(P);
-  g_launches.fetch_add(1);
-  return cuda_status(cudaGetLastError());
+  P.start = a.start; P.nstart = a.nstart;
+  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.status = a.status;
+  return mspe_run(P, L, G, static_cast<char *>(ws), a.idx, di, stream);
 }
 
 size_t select_mspe_batch_workspace_bytes(const BatchLaunch &b, int G) {
-  return mspe_layout(G, b.pmax, b.nmax, b.Mmax).total;
+  DevInfo di;
+  const int sms = dev_info(&di) == LAGP_OK ? di.num_sms : 152;
+  return mspe_layout(G, b.pmax, b.nmax, b.Mmax, b.T, b.idx_total, sms).total;
 }
 
 int select_mspe_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G,
@@ -459,38 +486,22 @@ int select_mspe_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, in
   if (st) return st;
   st = exp_table_upload();  // this translation unit's copy of the exp constants
   if (st) return st;
-  const MspeLayout L = mspe_layout(G, b.pmax, b.nmax, b.Mmax);
+  const MspeLayout L = mspe_layout(G, b.pmax, b.nmax, b.Mmax, b.T, b.idx_total, di.num_sms);
   if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
-  char *w = static_cast<char *>(ws);
   MspeParams P;
   P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
   P.M = b.Mmax; P.Mpad = (int)align_up((size_t)b.Mmax, 32); P.n0 = 0; P.n = b.nmax;
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;
   P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
-  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
-  P.queue = reinterpret_cast<int *>(w);
-  size_t off = 256;
-  P.U = reinterpret_cast<double *>(w + off); off += L.u;
-  P.Ud = reinterpret_cast<double *>(w + off); off += L.ud;
-  P.Xc = reinterpret_cast<double *>(w + off); off += L.xc;
-  P.cs = reinterpret_cast<double *>(w + off); off += L.cs;
-  P.Li = reinterpret_cast<double *>(w + off); off += L.nn;
-  P.Kd = reinterpret_cast<double *>(w + off); off += L.nn;
-  P.Kdd = reinterpret_cast<double *>(w + off); off += L.nn;
-  P.Q = reinterpret_cast<double *>(w + off); off += L.nn;
-  const size_t smem = mspe_smem_bytes(P.Mpad, b.nmax);
-  if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(select_mspe_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemsetAsync(P.queue, 0, sizeof(int), stream);
-  if (e != cudaSuccess) return cuda_status(e);
-  select_mspe_kernel<<<G, TB, smem, stream>>>(P);
-  g_launches.fetch_add(1);
-  return cuda_status(cudaGetLastError());
+  P.start = nullptr; P.nstart = 0;
+  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.status = b.status;
+  return mspe_run(P, L, G, static_cast<char *>(ws), b.idx, di, stream);
 }
 
-int select_mspe_prepare() { return exp_table_upload(); }
+int select_mspe_prepare() {
+  const int st = exp_table_upload();
+  return st ? st : predict_fp64_prepare();
+}
 
 }  // namespace lagp

@@ -82,6 +82,8 @@ def load(path: str | None = None):
                                          ctypes.c_uint32, P, sz, P]
     L.lagp_select_dev_noalloc.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
                                           i32, i32, P, P, P, P, P, P]
+    L.lagp_select_augment_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, P, i32, i32, f64, f64,
+                                          i32, i32, P, P, P, P, P, P, sz, P]
     L.lagp_select_theta_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, P, f64, i32,
                                         i32, P, P, P, P, P, P, sz, P]
     L.lagp_mle_workspace_bytes.argtypes = [i64, i32]
@@ -455,3 +457,15 @@ def predict_stagewise(X, Z, XX, n0, n, ncand, theta0, g, method="alc", precision
     lagp_design_predict_dev(X, Z, XX, idx, theta, g, mean, s2, var, status, ws_pr, stream)
     return dict(mean=mean, s2=s2, var=var, idx=idx, theta=theta, iters=iters, status=status,
                 mle_status=mstatus)
+
+
+def lagp_select_augment_dev(X, Z, XX, cand, start, n, theta, g, method, precision, mean, s2,
+                            var=None, idx=None, status=None, ws=None, stream=None) -> None:
+    """Kernels (b)+(c) growing saved designs start (T, n1) int32 to n points."""
+    N, p = X.shape
+    T, M = cand.shape
+    n1 = start.shape[1]
+    _chk(load().lagp_select_augment_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(cand), M, _dp(start),
+                                        n1, n, theta, g, _m(method), _pr(precision), _dp(mean),
+                                        _dp(s2), _dp(var), _dp(idx), _dp(status), _dp(ws),
+                                        ws.numel(), _stream(stream)), "lagp_select_augment_dev")

@@ -437,3 +437,50 @@ def test_mle_batch_matches_single():
     for t in range(3):
         th, it, st = oracle.mle(X, Z, idx[t], [0.2, 0.5, 2.0][t], 1e-4, 1e-3, 20.0)
         assert b["theta"][t] == th and b["iters"][t] == it and b["status"][t] == st
+
+
+# ---- design augmentation from a saved start design (Sec. 6)
+
+@pytest.mark.parametrize("method", ["alc", "mspe"])
+def test_augmenting_a_prefix_reproduces_the_design(method):
+    # the greedy choice depends only on the current design: growing the first n1 points of
+    # a design of size n back to n reproduces it, bit for bit
+    w = inputs.random_case(71, 400, 2, 3, 5, 16, 60, d=0.3, g=1e-4)
+    cand = oracle.knn(w.X, w.XX, w.ncand)
+    for t in range(w.T):
+        full = oracle.local_design(w.X, w.Z, w.XX[t], cand[t], w.n0, w.n, w.d, w.g, method)
+        assert full["status"] == 0
+        for n1 in (w.n0, 9, w.n - 1):
+            a = oracle.local_design(w.X, w.Z, w.XX[t], cand[t], 0, w.n, w.d, w.g, method,
+                                    start=full["idx"][:n1])
+            assert a["status"] == 0
+            assert np.array_equal(a["idx"], full["idx"])
+            assert a["mean"] == full["mean"] and a["s2"] == full["s2"]
+
+
+def test_augmenting_rejects_a_start_point_outside_the_candidates():
+    w = inputs.random_case(72, 400, 2, 1, 5, 16, 60, d=0.3, g=1e-4)
+    cand = oracle.knn(w.X, w.XX, w.ncand)[0]
+    outside = np.setdiff1d(np.arange(w.N), cand)[:1]
+    start = np.concatenate([cand[:4], outside]).astype(np.int32)
+    r = oracle.local_design(w.X, w.Z, w.XX[0], cand, 0, w.n, w.d, w.g, "alc", start=start)
+    assert r["status"] == oracle.INVALID
+    dup = np.array([cand[0], cand[1], cand[0]], np.int32)
+    r = oracle.local_design(w.X, w.Z, w.XX[0], cand, 0, w.n, w.d, w.g, "alc", start=dup)
+    assert r["status"] == oracle.INVALID
+
+
+def test_fp64_oracle_s2_error_within_the_cancellation_rounding_scale():
+    # the tolerance the parity protocol grants s2 in strongly cancelling cases
+    # (tests/parity.cancellation_bound) is met by the FP64 oracle itself against its
+    # long-double build, at every tiny-2d location
+    from tests.parity import cancellation_bound
+    w = inputs.tiny_2d()
+    cand = oracle.knn(w.X, w.XX, w.ncand)
+    worst = 0.0
+    for t in range(w.T):
+        o = oracle.local_design(w.X, w.Z, w.XX[t], cand[t], w.n0, w.n, w.d, w.g, "alc")
+        ld = oracle.design_predict(w.X, w.Z, w.XX[t], o["idx"], w.d, w.g, long_double=True)
+        e = abs(o["s2"] - ld[1]) / ld[1]
+        worst = max(worst, e / cancellation_bound(w, w.XX[t], o["idx"]))
+    assert worst <= 1.0, worst
