@@ -278,6 +278,22 @@ int lagp_select_augment_dev(const double *X, const double *Z, int64_t N, int32_t
                             double *var, int32_t *idx, int8_t *status, void *workspace,
                             size_t workspace_bytes, void *stream);
 
+/* Adaptive local design size (Sec. 6: a stopping criterion tracking the ratio of the
+ * predictive variance before and after each added point, V_j(x) / V_{j+1}(x), in which
+ * psi_j cancels): ALC designs grow from the n0 nearest as in lagp_select_dev, but stop
+ * before the first greedy point whose ratio v_j(x) / v_{j+1}(x) is below r_min (> 1), or
+ * at n points.  Outputs as lagp_select_dev, computed on each location's own design;
+ * n_out[t] (device, int32, required) gets its size n0 <= n_out[t] <= n (0 for a failed
+ * location); idx rows keep stride n, with -1 after n_out[t].  Rules as lagp_select_dev
+ * with n0 >= 3 (var needs n_out - 2 > 0), r_min > 1; the workspace is sized by
+ * lagp_select_workspace_bytes for LAGP_ALC. */
+int lagp_select_adaptive_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                             const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                             int32_t n0, int32_t n, double theta, double g, int32_t precision,
+                             double r_min, double *mean, double *s2, double *var, int32_t *idx,
+                             int32_t *n_out, int8_t *status, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
 /* ---- Local lengthscale estimates and the stagewise scheme (Sec. 4.2) ----
  * Sec. 4.2: (1) start from a global theta_0; (2) build each location's design with
  * theta_x; (3) estimate theta_x by maximum likelihood on that design; (4) set theta_x to

@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 
 ALC, MSPE, NN, MSPE_NODERIV = 0, 1, 2, 3
 METHODS = {"alc": ALC, "mspe": MSPE, "nn": NN}
-TRACE_W = 6
+TRACE_W = 7
 OK, INVALID, OOM, NOT_PD = 0, -1, -2, -5
 
 _lock = threading.Lock()
@@ -61,6 +61,8 @@ def _lib(long_double: bool = False):
             L.orc_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
             L.orc_local_design.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64, i32,
                                            P, P, P, P, P, P]
+            L.orc_local_design_adaptive.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64,
+                                                    f64, P, P, P, P, P, P, P]
             L.orc_local_design_start.argtypes = [P, P, i64, i32, P, P, i32, P, i32, i32, f64, f64,
                                                  i32, P, P, P, P, P, P]
             L.orc_predict.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32,
@@ -114,7 +116,7 @@ def knn(X, XX, M: int, nthreads: int = 0, with_d2: bool = False):
 
 
 def local_design(X, Z, x, cand, n0: int, n: int, d: float, g: float, method="alc",
-                 forced=None, long_double: bool = False, start=None):
+                 forced=None, long_double: bool = False, start=None, r_min=None):
     """Greedy local design and predictive equations at one location (Sec. 3; Eqs.
     dxy, mspe, predgp, preds2).  With start (n0 design indices) the design grows from
     that saved design instead of the n0 nearest (Sec. 6).  Returns dict(idx, mean, s2,
@@ -130,6 +132,15 @@ def local_design(X, Z, x, cand, n0: int, n: int, d: float, g: float, method="alc
     out = np.empty(3, np.float64)
     trace = np.full((max(n - n0, 1), TRACE_W), np.nan)
     fz = _i32(forced) if forced is not None else None
+    if r_min is not None:  # ALC with the stopping rule of Sec. 6
+        n_out = ctypes.c_int32()
+        st = _lib(long_double).orc_local_design_adaptive(
+            _p(X), _p(Z), N, p, _p(x), _p(cand), M, n0, n, d, g, r_min,
+            _p(fz) if fz is not None else None, _p(idx), _p(out[0:]), _p(out[1:]), _p(out[2:]),
+            _p(trace), ctypes.byref(n_out))
+        k = n_out.value
+        return dict(status=st, idx=idx, mean=out[0], s2=out[1], var=out[2], n_out=k,
+                    trace=trace[: max(k - n0 + 1, 0)])
     if start is not None:
         st = _lib(long_double).orc_local_design_start(
             _p(X), _p(Z), N, p, _p(x), _p(cand), M, _p(sz), n0, n, d, g, m,

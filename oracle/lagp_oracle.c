@@ -76,7 +76,7 @@ typedef double real;
 enum { ORC_ALC = 0, ORC_MSPE = 1, ORC_NN = 2, ORC_MSPE_NODERIV = 3 };
 
 /* Per greedy step, the trace holds these doubles (TRACE_W of them). */
-#define TRACE_W 6
+#define TRACE_W 7
 /* [0] best rank by the oracle's own criterion, [1] its score,
  * [2] chosen rank (== best unless a path is forced), [3] the chosen rank's score,
  * [4] second-best score, [5] v_j(x) before the step. */
@@ -430,8 +430,10 @@ static int mspe_prepare(const prob_t *P, work_t *W, const int32_t *cand, const d
  * idx_out: n design indices.  trace: (n-n0) x TRACE_W or NULL. */
 static int local_design(const prob_t *P, work_t *W, const double *x, const int32_t *cand,
                         int n0, int n, int method, const int32_t *forced, const int32_t *start,
-                        int32_t *idx_out, double *mean, double *s2, double *var, double *trace) {
+                        real r_min, int32_t *n_out, int32_t *idx_out, double *mean, double *s2,
+                        double *var, double *trace) {
   int M = W->M;
+  const int n_alloc = n;  /* idx_out's length; n shrinks if the stopping rule ends early */
   real onepg = 1 + P->g;
   memset(W->used, 0, (size_t)M);
   for (int c = 0; c < M; c++) W->kx[c] = corr_r(x, cand_pt(P, cand, c), P->p, P->theta);
@@ -541,12 +543,21 @@ static int local_design(const prob_t *P, work_t *W, const double *x, const int32
     }
     if (best < 0) return LAGP_ORC_NOT_PD;
     int chosen = forced ? forced_rank : best;
+    /* Sec. 6 stopping rule: v_j(x) / v_{j+1}(x), the chosen point's variance reduction
+     * ratio (psi cancels); the design stops before a point whose ratio is below r_min */
+    const real chosen_s = forced ? forced_s : best_s;
+    const real ratio = (method == ORC_ALC) ? vx / (vx - chosen_s) : NAN;
     if (trace) {
       double *tr = trace + (size_t)(j - n0) * TRACE_W;
       tr[0] = best; tr[1] = (double)best_s; tr[2] = chosen;
-      tr[3] = (double)(forced ? forced_s : best_s);
+      tr[3] = (double)chosen_s;
       tr[4] = have_second ? (double)second_s : NAN;
       tr[5] = (double)vx;
+      tr[6] = (double)ratio;
+    }
+    if (r_min > 0 && !forced && ratio < r_min) {
+      n = j;
+      break;
     }
     W->dr[j] = chosen;
     W->used[chosen] = 1;
@@ -571,6 +582,8 @@ static int local_design(const prob_t *P, work_t *W, const double *x, const int32
     vx = vx - W->ux[a] * W->ux[a];
   }
   for (int a = 0; a < n; a++) idx_out[a] = cand[W->dr[a]];
+  for (int a = n; a < n_alloc; a++) idx_out[a] = -1;
+  if (n_out) *n_out = n;
   *mean = (double)mu;
   *s2 = (double)(psi * vx / n);
   *var = (double)(psi * vx / (n - 2));
@@ -597,7 +610,8 @@ int orc_local_design(const double *X, const double *Z, int64_t N, int32_t p, con
   prob_t P = {X, Z, N, p, (real)theta, (real)g};
   work_t W;
   if (work_alloc(&W, n, M)) return LAGP_ORC_OOM;
-  st = local_design(&P, &W, x, cand, n0, n, method, forced, NULL, idx, mean, s2, var, trace);
+  st = local_design(&P, &W, x, cand, n0, n, method, forced, NULL, 0, NULL, idx, mean, s2, var,
+                    trace);
   work_free(&W);
   return st;
 }
@@ -616,7 +630,30 @@ int orc_local_design_start(const double *X, const double *Z, int64_t N, int32_t 
   prob_t P = {X, Z, N, p, (real)theta, (real)g};
   work_t W;
   if (work_alloc(&W, n, M)) return LAGP_ORC_OOM;
-  st = local_design(&P, &W, x, cand, n1, n, method, forced, start, idx, mean, s2, var, trace);
+  st = local_design(&P, &W, x, cand, n1, n, method, forced, start, 0, NULL, idx, mean, s2, var,
+                    trace);
+  work_free(&W);
+  return st;
+}
+
+/* orc_local_design with the stopping rule of Sec. 6 (ALC): the design stops growing
+ * before the first greedy point whose variance-reduction ratio v_j(x) / v_{j+1}(x) is
+ * below r_min (> 1), and at n at the latest; *n_out gets its size, idx the n_out indices
+ * followed by -1.  With forced, the path is replayed in full and only traced (field 6
+ * of each trace row is the ratio). */
+int orc_local_design_adaptive(const double *X, const double *Z, int64_t N, int32_t p,
+                              const double *x, const int32_t *cand, int32_t M, int32_t n0,
+                              int32_t n, double theta, double g, double r_min,
+                              const int32_t *forced, int32_t *idx, double *mean, double *s2,
+                              double *var, double *trace, int32_t *n_out) {
+  int st = check_args(N, p, 1, n0, n, M, theta, g, ORC_ALC);
+  if (st) return st;
+  if (n0 < 3 || !(r_min > 1)) return LAGP_ORC_INVALID;
+  prob_t P = {X, Z, N, p, (real)theta, (real)g};
+  work_t W;
+  if (work_alloc(&W, n, M)) return LAGP_ORC_OOM;
+  st = local_design(&P, &W, x, cand, n0, n, ORC_ALC, forced, NULL, (real)r_min, n_out, idx, mean,
+                    s2, var, trace);
   work_free(&W);
   return st;
 }
@@ -648,7 +685,7 @@ int orc_predict(const double *X, const double *Z, int64_t N, int32_t p, const do
 #pragma omp for schedule(dynamic, 1)
     for (int64_t t = 0; t < T; t++) {
       if (!ok) continue;
-      int s = local_design(&P, &W, XX + t * p, cand + t * M, n0, n, method, NULL, NULL,
+      int s = local_design(&P, &W, XX + t * p, cand + t * M, n0, n, method, NULL, NULL, 0, NULL,
                            idx + t * n, mean + t, s2 + t, var + t, NULL);
       status[t] = s;
       if (s) { mean[t] = NAN; s2[t] = NAN; var[t] = NAN; }

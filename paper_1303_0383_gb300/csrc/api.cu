@@ -173,7 +173,7 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
   a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
-  a.start = nullptr; a.nstart = 0;
+  a.start = nullptr; a.nstart = 0; a.r_min = 0.0; a.n_out = nullptr;
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
@@ -295,8 +295,29 @@ int lagp_select_augment_dev(const double *X, const double *Z, int64_t N, int32_t
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
   a.M = ncand; a.n0 = n1; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
-  a.start = start; a.nstart = n1;
+  a.start = start; a.nstart = n1; a.r_min = 0.0; a.n_out = nullptr;
   a.method = method; a.precision = precision;
+  a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
+  return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int lagp_select_adaptive_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                             const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                             int32_t n0, int32_t n, double theta, double g, int32_t precision,
+                             double r_min, double *mean, double *s2, double *var, int32_t *idx,
+                             int32_t *n_out, int8_t *status, void *workspace,
+                             size_t workspace_bytes, void *stream) {
+  int st = check_common(N, p, T, n0, n, ncand, theta, g, LAGP_ALC, precision);
+  if (st) return st;
+  if (n0 < 3 || !(r_min > 1.0) || !isfinite(r_min)) return LAGP_ERR_INVALID_ARG;
+  if (T > 0 && (!X || !Z || !XX || !cand || !mean || !s2 || !n_out || !workspace))
+    return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  SelectArgs a;
+  a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
+  a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
+  a.start = nullptr; a.nstart = 0; a.r_min = r_min; a.n_out = n_out;
+  a.method = LAGP_ALC; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
 }
@@ -316,7 +337,7 @@ int lagp_select_theta_dev(const double *X, const double *Z, int64_t N, int32_t p
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
   a.M = ncand; a.n0 = n0; a.n = n; a.theta = 1.0; a.g = g; a.theta_loc = theta;
-  a.start = nullptr; a.nstart = 0;
+  a.start = nullptr; a.nstart = 0; a.r_min = 0.0; a.n_out = nullptr;
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
@@ -365,7 +386,7 @@ int lagp_design_predict_dev(const double *X, const double *Z, int64_t N, int32_t
   if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
   PredictArgs a;
   a.X = X; a.Z = Z; a.p = p; a.XX = XX; a.T = T; a.n = n; a.nmax = n; a.theta = theta; a.g = g;
-  a.idx = idx; a.B = BatchView{nullptr, nullptr, nullptr, 0, theta_loc};
+  a.idx = idx; a.B = BatchView{nullptr, nullptr, nullptr, 0, theta_loc, nullptr};
   a.mean = mean; a.s2 = s2; a.var = var; a.status = status;
   return predict_fp64_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
 }

@@ -31,6 +31,7 @@ struct BatchView {
   const int32_t *order;        // queue position -> location (cost-sorted), may be nullptr
   int ldxx;                    // row stride of XX in doubles
   const double *theta_loc;     // per-location lengthscale (T), or nullptr
+  const int32_t *n_loc;        // per-location design size (T, adaptive designs), or nullptr
 };
 
 // A location's parameters, resolved from the tables or the uniform values.
@@ -69,6 +70,7 @@ __device__ __forceinline__ LocParams resolve_loc(const BatchView &B, int64_t q, 
     L.theta = B.theta_loc[L.loc];
     L.theta_inv = 1.0 / L.theta;
   }
+  if (B.n_loc) L.n = B.n_loc[L.loc];  // an adaptive design's size (idx keeps the launch stride)
   return L;
 }
 

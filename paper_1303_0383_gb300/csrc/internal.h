@@ -52,6 +52,8 @@ struct SelectArgs {
   const double *theta_loc;  // per-location lengthscale (device, T), or nullptr: theta
   const int32_t *start;     // saved start designs (device, T x nstart), or nullptr: n0 nearest
   int32_t nstart;
+  double r_min;             // > 1: stopping rule of Sec. 6 (ALC), 0: fixed n
+  int32_t *n_out;           // adaptive designs' sizes (device, T), with r_min
   int32_t method, precision;
   double *mean, *s2, *var;
   int32_t *idx;

@@ -70,7 +70,7 @@ extern "C" int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t
   SelectArgs a;
   a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
   a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
-  a.start = nullptr; a.nstart = 0;
+  a.start = nullptr; a.nstart = 0; a.r_min = 0.0; a.n_out = nullptr;
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch_on_grid(a, scratch, cap, G, static_cast<cudaStream_t>(stream));

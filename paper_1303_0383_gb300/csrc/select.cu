@@ -58,6 +58,8 @@ struct SelParams {
   BatchView B;    // per-location tables (B.designs == nullptr: uniform launch)
   const int32_t *start;  // saved start designs (T x nstart design indices), or nullptr
   int nstart;
+  double r_min;          // > 1: stopping rule of Sec. 6 (ALC); 0: the design has n points
+  int32_t *n_out;        // design sizes (T) when r_min > 1
 };
 
 // ALC scores are compared as fractions cov^2 / v without dividing: a/da beats b/db when
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
   __shared__ int red_r[SB / 32];
   __shared__ double etab[64];
   if (threadIdx.x < 64) etab[threadIdx.x] = c_exp.tab[threadIdx.x];
-  __shared__ int sh_loc, sh_best, sh_fail;
+  __shared__ int sh_loc, sh_best, sh_fail, sh_n;
   __shared__ double sh_inv, sh_uxj, sh_vx, sh_psi;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
     const int n = L.n, p = L.p, M = L.M;
     const int32_t *cnd = L.cand;
     if (tid < p) xl[tid] = L.x[tid];
-    if (tid == 0) { sh_fail = 0; sh_vx = L.onepg; sh_psi = 0.0; }
+    if (tid == 0) { sh_fail = 0; sh_vx = L.onepg; sh_psi = 0.0; sh_n = n; }
     __syncthreads();
     // the start design: the n0 nearest, or a saved design (augmentation)
     const int n0e = P.start ? P.nstart : L.n0;
@@ -143,20 +145,28 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         } else {
           const double sq = sqrt(vs);
           const double uxj = covx[s] / sq;                 // u_x[j]
-          double t = L.Z[cnd[s]];
-          for (int i = 0; i < j; i++) t = fma(-srow[i], yt[i], t);
-          const double ytj = t / sq;                       // ytil[j]
-          ux[j] = uxj;
-          yt[j] = ytj;
-          sh_vx = fma(-uxj, uxj, sh_vx);
-          sh_psi = fma(ytj, ytj, sh_psi);
-          sh_inv = 1.0 / sq;
-          sh_uxj = uxj;
-          used[s] = 1;
-          if (L.idx) L.idx[j] = cnd[s];
+          const double vxn = fma(-uxj, uxj, sh_vx);       // v_{j+1}(x)
+          if (P.r_min > 0.0 && j >= n0e && sh_vx / vxn < P.r_min) {
+            // Sec. 6 stopping rule: the design stops before a greedy point whose variance
+            // reduction ratio v_j(x) / v_{j+1}(x) (psi cancels) is below r_min
+            sh_n = j;
+          } else {
+            double t = L.Z[cnd[s]];
+            for (int i = 0; i < j; i++) t = fma(-srow[i], yt[i], t);
+            const double ytj = t / sq;                     // ytil[j]
+            ux[j] = uxj;
+            yt[j] = ytj;
+            sh_vx = vxn;
+            sh_psi = fma(ytj, ytj, sh_psi);
+            sh_inv = 1.0 / sq;
+            sh_uxj = uxj;
+            used[s] = 1;
+            if (L.idx) L.idx[j] = cnd[s];
+          }
         }
       }
       __syncthreads();
+      if (sh_n == j) break;
       if (sh_fail) break;
       if (j == n - 1) break;
       const double inv = sh_inv, uxj = sh_uxj;
@@ -209,7 +219,9 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
       __syncthreads();
     }
     __syncthreads();
+    const int ne = sh_n;  // the design's size (n, or where the stopping rule ended it)
     if (tid == 0) {
+      if (P.n_out) P.n_out[loc] = sh_fail ? 0 : ne;
       if (sh_fail) {
         if (P.status) P.status[loc] = (int8_t)LAGP_ERR_NOT_PD;
         P.mean[loc] = NAN;
@@ -217,17 +229,19 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
         if (P.var) P.var[loc] = NAN;
       } else {
         double mu = 0.0;
-        for (int i = 0; i < n; i++) mu = fma(ux[i], yt[i], mu);
+        for (int i = 0; i < ne; i++) mu = fma(ux[i], yt[i], mu);
         const double pv = sh_psi * sh_vx;
         P.mean[loc] = mu;
-        P.s2[loc] = pv / n;
-        if (P.var) P.var[loc] = pv / (n - 2);
+        P.s2[loc] = pv / ne;
+        if (P.var) P.var[loc] = pv / (ne - 2);
         if (P.status) P.status[loc] = 0;
       }
     }
-    if (sh_fail && L.idx) {
-      // A failed location reports no design: every index is -1.
-      for (int i = tid; i < n; i += SB) L.idx[i] = -1;
+    if (L.idx) {
+      // A failed location reports no design: every index is -1; an adaptive design's
+      // unused slots are -1 too.
+      for (int i = tid; i < n; i += SB)
+        if (sh_fail || i >= ne) L.idx[i] = -1;
     }
   }
 }
@@ -279,8 +293,9 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   P.g = a.g;
   P.nmax = a.n;
   P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc, nullptr};
   P.start = a.start; P.nstart = a.nstart;
+  P.r_min = a.r_min; P.n_out = a.n_out;
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -324,8 +339,9 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   P.g = a.g;
   P.nmax = a.n;
   P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc, nullptr};
   P.start = a.start; P.nstart = a.nstart;
+  P.r_min = a.r_min; P.n_out = a.n_out;
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.idx = a.idx; P.status = a.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);
@@ -381,8 +397,9 @@ int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStr
   P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
   P.M = b.Mmax; P.Mpad = Mpad; P.n0 = 0; P.n = b.nmax; P.method = b.method;
   P.theta = 1.0; P.g = 0.0; P.nmax = b.nmax; P.pmax = b.pmax;
-  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr, nullptr};
   P.start = nullptr; P.nstart = 0;
+  P.r_min = 0.0; P.n_out = nullptr;
   P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.idx = b.idx; P.status = b.status;
   P.queue = reinterpret_cast<int *>(w);
   P.U = reinterpret_cast<double *>(w + 256);

@@ -52,6 +52,8 @@ struct MixParams {
   int *rescores; // count of FP64 re-score passes (diagnostics)
   const int32_t *start;  // saved start designs (T x nstart design indices), or nullptr
   int nstart;
+  double r_min;          // > 1: stopping rule of Sec. 6; 0: the design has n points
+  int32_t *n_out;        // design sizes (T) when r_min > 1
 };
 
 #ifndef LAGP_MIX_MINB
@@ -146,6 +148,8 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     if (P.start) start_ranks(P.start + L.loc * P.nstart, P.nstart, cnd, M, dr);
 
     int best = 0;
+    int ne = n;       // the design's size (n, or where the stopping rule ends it)
+    ff vx = onepg;    // v_j(x), carried by every thread for the stopping rule
     for (int j = 0; j < n; j++) {
       const int s = (j < n0e) ? (P.start ? dr[j] : j) : best;
       if (s < 0) {  // nothing admissible left (the same for every thread)
@@ -160,6 +164,16 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       // every thread derives the step's scalars itself: no barrier needed for them
       const ff inv = ff_rcp(ff_sqrt(vs));
       const ff uxj = ff_mul(ff2_get(cp, s), inv);
+      if (P.r_min > 0.0) {
+        // Sec. 6 stopping rule: stop before a greedy point whose variance reduction ratio
+        // v_j(x) / v_{j+1}(x) (psi cancels) is below r_min; every thread decides alike
+        const ff vxn = ff_sub(vx, ff_mul(uxj, uxj));
+        if (j >= n0e && ff_to_double(vx) / ff_to_double(vxn) < P.r_min) {
+          ne = j;
+          break;
+        }
+        vx = vxn;
+      }
       if (tid == 0) dr[j] = s;
       if (tid == ((s >> 1) % MB)) used[s] = 1;  // the pair's owner keeps the flags
       // this warp's copy of the new factor row u_s and of x_s (relative to x)
@@ -222,7 +236,8 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     __syncthreads();
     // the design (design indices), or -1 when a step failed; kernel (c) (predict.cu)
     // evaluates the predictive equations on it in FP64
-    for (int i = tid; i < n; i += MB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
+    for (int i = tid; i < n; i += MB) L.idx[i] = (sh_fail || i >= ne) ? -1 : cnd[dr[i]];
+    if (P.n_out && tid == 0) P.n_out[L.loc] = sh_fail ? 0 : ne;
     // The factor rows in global memory are dead now (the next location rewrites each row
     // before reading it): drop their L2 lines without writing them back to DRAM.
     {
@@ -314,6 +329,7 @@ int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, ch
   if (e != cudaSuccess) return cuda_status(e);
   PredictArgs pa = pa_in;
   pa.idx = P.idx;
+  pa.B.n_loc = P.n_out;  // adaptive designs: kernel (c) on each location's own size
   return predict_fp64_launch(pa, o, L.pred, stream);
 }
 
@@ -338,8 +354,9 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   P.M = a.M; P.Mpad = mix_mpad(a.M); P.Qpad = P.Mpad / 2; P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc, nullptr};
   P.start = a.start; P.nstart = a.nstart;
+  P.r_min = a.r_min; P.n_out = a.n_out;
   PredictArgs pa;
   pa.X = a.X; pa.Z = a.Z; pa.p = a.p; pa.XX = a.XX; pa.T = a.T; pa.n = a.n; pa.nmax = a.n;
   pa.theta = a.theta; pa.g = a.g; pa.idx = nullptr; pa.B = P.B;
@@ -367,8 +384,9 @@ int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, i
   P.M = b.Mmax; P.Mpad = mix_mpad(b.Mmax); P.Qpad = P.Mpad / 2; P.n0 = 0; P.n = b.nmax;
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;
-  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr, nullptr};
   P.start = nullptr; P.nstart = 0;
+  P.r_min = 0.0; P.n_out = nullptr;
   PredictArgs pa;
   pa.X = nullptr; pa.Z = nullptr; pa.p = b.pmax; pa.XX = b.XX; pa.T = b.T; pa.n = b.nmax;
   pa.nmax = b.nmax; pa.theta = 1.0; pa.g = 0.0; pa.idx = nullptr; pa.B = P.B;

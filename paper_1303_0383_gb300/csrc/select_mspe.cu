@@ -467,7 +467,7 @@ int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStrea
   P.M = a.M; P.Mpad = (int)align_up((size_t)a.M, 32); P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
-  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc};
+  P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc, nullptr};
   P.start = a.start; P.nstart = a.nstart;
   P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.status = a.status;
   return mspe_run(P, L, G, static_cast<char *>(ws), a.idx, di, stream);
@@ -493,7 +493,7 @@ int select_mspe_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, in
   P.M = b.Mmax; P.Mpad = (int)align_up((size_t)b.Mmax, 32); P.n0 = 0; P.n = b.nmax;
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;
-  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr};
+  P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr, nullptr};
   P.start = nullptr; P.nstart = 0;
   P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.status = b.status;
   return mspe_run(P, L, G, static_cast<char *>(ws), b.idx, di, stream);

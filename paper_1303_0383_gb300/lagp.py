@@ -82,6 +82,8 @@ def load(path: str | None = None):
                                          ctypes.c_uint32, P, sz, P]
     L.lagp_select_dev_noalloc.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
                                           i32, i32, P, P, P, P, P, P]
+    L.lagp_select_adaptive_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64,
+                                           i32, f64, P, P, P, P, P, P, P, sz, P]
     L.lagp_select_augment_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, P, i32, i32, f64, f64,
                                           i32, i32, P, P, P, P, P, P, sz, P]
     L.lagp_select_theta_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, P, f64, i32,
@@ -469,3 +471,14 @@ def lagp_select_augment_dev(X, Z, XX, cand, start, n, theta, g, method, precisio
                                         n1, n, theta, g, _m(method), _pr(precision), _dp(mean),
                                         _dp(s2), _dp(var), _dp(idx), _dp(status), _dp(ws),
                                         ws.numel(), _stream(stream)), "lagp_select_augment_dev")
+
+
+def lagp_select_adaptive_dev(X, Z, XX, cand, n0, n, theta, g, precision, r_min, mean, s2, n_out,
+                             var=None, idx=None, status=None, ws=None, stream=None) -> None:
+    """ALC designs with the stopping rule of Sec. 6 (sizes into n_out (T,) int32)."""
+    N, p = X.shape
+    T, M = cand.shape
+    _chk(load().lagp_select_adaptive_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(cand), M, n0, n,
+                                         theta, g, _pr(precision), r_min, _dp(mean), _dp(s2),
+                                         _dp(var), _dp(idx), _dp(n_out), _dp(status), _dp(ws),
+                                         ws.numel(), _stream(stream)), "lagp_select_adaptive_dev")

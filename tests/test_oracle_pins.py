@@ -484,3 +484,31 @@ def test_fp64_oracle_s2_error_within_the_cancellation_rounding_scale():
         e = abs(o["s2"] - ld[1]) / ld[1]
         worst = max(worst, e / cancellation_bound(w, w.XX[t], o["idx"]))
     assert worst <= 1.0, worst
+
+
+# ---- adaptive design size: the stopping rule of Sec. 6 (ALC)
+
+def test_stopping_rule_definition_and_monotonicity():
+    w = inputs.tiny_2d()
+    cand = oracle.knn(w.X, w.XX, w.ncand)
+    for t in (0, 17, 55, 99):
+        full = oracle.local_design(w.X, w.Z, w.XX[t], cand[t], w.n0, w.n, w.d, w.g, "alc")
+        # the ratio v_j(x)/v_{j+1}(x) of each chosen point, from the trace
+        vx, sc = full["trace"][:, 5], full["trace"][:, 3]
+        ratio = vx / (vx - sc)
+        assert np.allclose(ratio, full["trace"][:, 6], rtol=1e-12)
+        assert (ratio >= 1).all()
+        prev = w.n
+        for r_min in (1.0001, 1.001, 1.01, 1.1, 2.0):
+            a = oracle.local_design(w.X, w.Z, w.XX[t], cand[t], w.n0, w.n, w.d, w.g, "alc",
+                                    r_min=r_min)
+            k = a["n_out"]
+            assert a["status"] == 0 and w.n0 <= k <= prev
+            prev = k
+            # the first k points are the fixed-size design's; its first step below r_min is k
+            assert np.array_equal(a["idx"][:k], full["idx"][:k]) and (a["idx"][k:] == -1).all()
+            below = np.nonzero(ratio < r_min)[0]
+            assert k == (w.n0 + below[0] if len(below) else w.n)
+            # predictions are those of the k-point design
+            m, s2, v = oracle.design_predict(w.X, w.Z, w.XX[t], a["idx"][:k], w.d, w.g)
+            assert abs(a["mean"] - m) <= 1e-12 * abs(m) and abs(a["s2"] - s2) <= 1e-9 * s2
