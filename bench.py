@@ -307,10 +307,23 @@ def time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method="
                 mean=mean.cpu().numpy(), s2=s2.cpu().numpy())
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of floats over the ranks of the process group (the
+    slowest rank's time is the job's); the values themselves when not distributed."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def barrier(torch):
     if torch.distributed.is_available() and torch.distributed.is_initialized():
         torch.distributed.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
 
 def roofline_for(prec, w, sel_ms, traffic, method="alc"):
@@ -530,10 +543,8 @@ def run_gpu(args):
 
     for k, r in res.items():
         if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([r["ms"], r["e2e_ms"], r["sel_ms"]], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            r["ms"], r["e2e_ms"], r["sel_ms"] = float(tt[0]), float(tt[1]), float(tt[2])
+            r["ms"], r["e2e_ms"], r["sel_ms"] = max_over_ranks([r["ms"], r["e2e_ms"], r["sel_ms"]],
+                                                               dev)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
