@@ -256,3 +256,13 @@ def test_mspe_mixed_is_refused():
     with pytest.raises(lagp.LagpError) as e:
         lagp.predict_torch(X, Z, XX, w.n0, w.n, w.ncand, w.d, w.g, "mspe", "mixed")
     assert e.value.code == lagp.LAGP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64")])
+def test_smooth_8d_full_size_sampled(method, precision):
+    # the 8-d workload in the benchmark's launch configuration (10000 locations, n = 100,
+    # 2000 candidates); the oracle checks a seeded sample
+    w = inputs.smooth_8d()
+    locs = np.random.default_rng(9).choice(w.T, size=10, replace=False)
+    g, infos, bad = run_parity(w, locs=locs, method=method, precision=precision)
+    assert not bad, bad[:3]
