@@ -157,7 +157,13 @@ std::string signature(const Plan &P, int32_t method, int32_t precision, int64_t 
 
 // ---- graph cache: one instantiated graph per (signature, buffers, launch shape)
 std::mutex g_graph_mu;
-std::map<std::string, cudaGraphExec_t> g_graphs;
+// An instantiated graph and the number of kernels it launches (counted at capture, where
+// the launches are recorded but do not run; added to the launch counter at each replay).
+struct GraphEntry {
+  cudaGraphExec_t exec;
+  int64_t kernels;
+};
+std::map<std::string, GraphEntry> g_graphs;
 
 // One non-blocking stream per device for graph capture (created on first use).
 cudaStream_t capture_stream(int device) {
@@ -301,10 +307,14 @@ extern "C" int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t n
       k += dk;
     }
     cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
     {
       std::lock_guard<std::mutex> lk(g_graph_mu);
       auto it = g_graphs.find(k);
-      if (it != g_graphs.end()) exec = it->second;
+      if (it != g_graphs.end()) {
+        exec = it->second.exec;
+        kernels = it->second.kernels;
+      }
     }
     if (!exec) {
       // Capture on a library-owned stream (the legacy default stream cannot be captured);
@@ -318,8 +328,11 @@ extern "C" int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t n
       cudaGraph_t graph;
       e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_status(e);
+      const int64_t before = g_launches.load();
       st = launch_all(P, L, w, XX, ldxx, T, method, precision, mean, s2, var, idx, status,
                       knn_ctas, sel_ctas, cap);
+      kernels = g_launches.load() - before;
+      g_launches.fetch_sub(kernels);  // recorded, not run
       e = cudaStreamEndCapture(cap, &graph);
       if (st) return st;
       if (e != cudaSuccess) return cuda_status(e);
@@ -327,9 +340,10 @@ extern "C" int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t n
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_status(e);
       std::lock_guard<std::mutex> lk(g_graph_mu);
-      g_graphs[k] = exec;
+      g_graphs[k] = GraphEntry{exec, kernels};
     }
     e = cudaGraphLaunch(exec, stream);
+    if (e == cudaSuccess) g_launches.fetch_add(kernels);
     return cuda_status(e);
   }
   return launch_all(P, L, w, XX, ldxx, T, method, precision, mean, s2, var, idx, status, knn_ctas,
