@@ -71,6 +71,26 @@ __device__ __forceinline__ ff ff_sub_prod_acc(ff acc, ff a, ff b) {
   return fast_two_sum(s.h, __fsub_rn(__fadd_rn(s.l, acc.l), e));
 }
 
+// Compensated dot product of float-float vectors: the running sum stays FP32 and every
+// rounding error (TwoProd of the high parts with the cross terms, TwoSum of the running
+// sum) is collected in a second FP32 sum (Dot2 of Ogita, Rump and Oishi, 2005, extended to
+// float-float operands); the result is h + l.
+struct ffacc {
+  float h, l;
+};
+
+__device__ __forceinline__ void ffacc_add_prod(ffacc &acc, ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);  // a b - p to FP32 accuracy
+  const float s = __fadd_rn(acc.h, p);
+  const float bb = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+  acc.h = s;
+}
+
 // sqrt and reciprocal by one Newton correction of the FP32 estimate.
 __device__ __forceinline__ ff ff_sqrt(ff a) {
   const float s = sqrtf(a.h);

@@ -17,14 +17,16 @@
 // tol * theta (the new point is returned), when l' = 0, or at an end of [tmin, tmax]
 // where l' points outward.
 //
-// One CTA per location, FP64 throughout (K^-1 has large entries of both signs, so the
-// products below cancel: FP32 would leave l'' without a correct digit).  Per iteration:
-// K and Kd (one exp per pair), the Cholesky factor (fp64_chol.cuh), L^-1 by forward
-// substitution row by row, K^-1 = L^-T L^-1, the product K^-1 Kd for tr((K^-1 Kd)^2)
-// (n^3, the largest term), then O(n^2) vector work.  The matrices live in shared memory
+// One CTA per location.  Per iteration, in FP64: K and Kd (one exp per pair), the
+// Cholesky factor (fp64_chol.cuh), L^-1 by forward substitution row by row,
+// K^-1 = L^-T L^-1 and the O(n^2) vector terms; the n^3 product K^-1 Kd behind
+// tr((K^-1 Kd)^2) runs in float-float on the FP32 pipes (K^-1 has large entries of both
+// signs, so plain FP32 would leave l'' without a correct digit; float-float keeps about
+// 48 bits per product).  The matrices live in shared memory
 // when they fit, else in a per-CTA slot of the workspace.
 #include <math.h>
 
+#include "ff.cuh"
 #include "fp64_chol.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
@@ -194,17 +196,31 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
         t3 += st3;
       }
       __syncthreads();
-      // tr((K^-1 Kd)^2) = sum_ab A_ab A_ba with A = K^-1 Kd: each (a <= b) pair forms both
-      double t2p = 0.0;
+      // tr((K^-1 Kd)^2) = sum_ab A_ab A_ba with A = K^-1 Kd, the n^3 term: formed in
+      // float-float on the FP32 pipes (compensated dots, about 2^-48 per product).  It
+      // enters l'' only, which sets the Newton step, not the root l' = 0 the iteration
+      // converges to.  K^-1 goes to L^-1's storage (no longer needed) and Kd is converted
+      // in place (its FP64 uses are done), one float-float pair per FP64 slot.
+      float2 *Kif = reinterpret_cast<float2 *>(Lm), *Kdf = reinterpret_cast<float2 *>(Kd);
       for (int e = tid; e < n * n; e += LB) {
+        const ff ki = ff_from_double(Ki[e]), kd = ff_from_double(Kd[e]);
+        Kif[e] = make_float2(ki.h, ki.l);
+        Kdf[e] = make_float2(kd.h, kd.l);
+      }
+      __syncthreads();
+      double t2p = 0.0;
+      for (int e = tid; e < n * n; e += LB) {  // each (a <= b) pair forms A_ab and A_ba
         const int a = e / n, b = e % n;
         if (b < a) continue;
-        double sab = 0.0, sba = 0.0;
+        ffacc sab{0.0f, 0.0f}, sba{0.0f, 0.0f};
         for (int m = 0; m < n; m++) {
-          sab = fma(Ki[a * lda + m], Kd[m * lda + b], sab);
-          sba = fma(Ki[b * lda + m], Kd[m * lda + a], sba);
+          const float2 x1 = Kif[a * lda + m], y1 = Kdf[m * lda + b];
+          const float2 x2 = Kif[b * lda + m], y2 = Kdf[m * lda + a];
+          ffacc_add_prod(sab, ff{x1.x, x1.y}, ff{y1.x, y1.y});
+          ffacc_add_prod(sba, ff{x2.x, x2.y}, ff{y2.x, y2.y});
         }
-        t2p = fma((a == b ? 1.0 : 2.0) * sab, sba, t2p);
+        const double vab = (double)sab.h + (double)sab.l, vba = (double)sba.h + (double)sba.l;
+        t2p = fma((a == b ? 1.0 : 2.0) * vab, vba, t2p);
       }
       psi = block_sum(psi, red);
       q3 = block_sum(q3, red);
