@@ -257,62 +257,60 @@ __device__ __forceinline__ float sqdist_f32(const float *xf, const float *xi, in
   return acc;
 }
 
-constexpr int NBUCKET = 2048;  // buckets of the survivors' order (half of the histogram)
 constexpr int BUCKET_CAP = 32; // largest bucket sorted in place; beyond, the bitonic sort
 
 // Rank order of the cnt survivors (keys (d2 hi, d2 lo, index) in kh/kl/sidx) by a bucket
-// sort: d2 * (NBUCKET - 1) / max d2 is monotone in d2, so buckets in index order hold
+// sort: floor(d2 (nb - 1) / max d2) is monotone in d2, so buckets in index order hold
 // increasing distances; each bucket is then put in exact key order by insertion (buckets
-// hold one or two survivors on average).  Writes the first M indices to out and returns
-// true; returns false (nothing written) when cnt exceeds the histogram's second half or
-// a bucket holds more than BUCKET_CAP survivors (many equal distances), leaving the keys
-// for the bitonic sort.  Uses hist[0, NBUCKET) for the bucket bounds and
-// hist[NBUCKET, 2 NBUCKET) for the permutation.  Every thread returns after the same
-// barriers.
+// hold a few survivors on average).  Writes the first M indices to out and returns true;
+// returns false (nothing written) when a bucket holds more than BUCKET_CAP survivors
+// (many equal distances), leaving the keys for the bitonic sort.  The bucket bounds use
+// hist[0, nb); the permutation goes to perm (cnt entries), which may be hist + nb.
+// Every thread returns after the same barriers.
 __device__ bool bucket_order(const uint32_t *kh, const uint32_t *kl, const int32_t *sidx, int cnt,
-                             int M, uint32_t *hist, uint32_t *warp_tmp, uint32_t *sh_flag,
-                             unsigned long long *sh_dmax, int32_t *out) {
-  if (cnt > NBUCKET) return false;  // the same for every thread
-  uint32_t *bound = hist, *perm = hist + NBUCKET;
+                             int M, uint32_t *hist, int nb, uint32_t *perm, uint32_t *warp_tmp,
+                             uint32_t *sh_flag, unsigned long long *sh_dmax, int32_t *out) {
+  uint32_t *bound = hist;
   if (threadIdx.x == 0) {
     *sh_dmax = 0ull;
     *sh_flag = 0u;
   }
-  for (int b = threadIdx.x; b < NBUCKET; b += KB) bound[b] = 0;
+  for (int b = threadIdx.x; b < nb; b += KB) bound[b] = 0;
   __syncthreads();
   for (int r = threadIdx.x; r < cnt; r += KB)
     atomicMax(sh_dmax, ((unsigned long long)kh[r] << 32) | kl[r]);  // non-negative doubles order like their bits
   __syncthreads();
   const double dmax = __longlong_as_double((long long)*sh_dmax);
   if (!(dmax > 0.0)) return false;
-  const double scale = (double)(NBUCKET - 1) / dmax;
+  const double scale = (double)(nb - 1) / dmax;
   auto bucket_of = [&](int r) {
     const double d2 = __longlong_as_double((long long)(((unsigned long long)kh[r] << 32) | kl[r]));
     const int b = (int)(d2 * scale);
-    return b < NBUCKET - 1 ? b : NBUCKET - 1;
+    return b < nb - 1 ? b : nb - 1;
   };
   for (int r = threadIdx.x; r < cnt; r += KB) atomicAdd(&bound[bucket_of(r)], 1u);
   __syncthreads();
-  // exclusive scan of the counts (eight buckets per thread), flagging an oversized bucket
-  constexpr int PER = NBUCKET / KB;
-  uint32_t c[PER], part = 0;
-  for (int k = 0; k < PER; k++) {
-    c[k] = bound[threadIdx.x * PER + k];
-    part += c[k];
-    if (c[k] > BUCKET_CAP) *sh_flag = 1u;
+  // exclusive scan of the counts (nb / KB buckets per thread), flagging an oversized bucket
+  const int per = nb / KB;
+  uint32_t part = 0;
+  for (int k = 0; k < per; k++) {
+    const uint32_t c = bound[threadIdx.x * per + k];
+    part += c;
+    if (c > BUCKET_CAP) *sh_flag = 1u;
   }
   uint32_t total;
   uint32_t run = block_excl_scan(part, warp_tmp, &total);
-  for (int k = 0; k < PER; k++) {
-    bound[threadIdx.x * PER + k] = run;
-    run += c[k];
+  for (int k = 0; k < per; k++) {
+    const uint32_t c = bound[threadIdx.x * per + k];
+    bound[threadIdx.x * per + k] = run;
+    run += c;
   }
   __syncthreads();
   if (*sh_flag) return false;
   // scatter: afterwards bound[b] is the end of bucket b (= the start of bucket b + 1)
   for (int r = threadIdx.x; r < cnt; r += KB) perm[atomicAdd(&bound[bucket_of(r)], 1u)] = r;
   __syncthreads();
-  for (int b = threadIdx.x; b < NBUCKET; b += KB) {
+  for (int b = threadIdx.x; b < nb; b += KB) {
     const uint32_t lo = b ? bound[b - 1] : 0u, hi = bound[b];
     for (uint32_t i = lo + 1; i < hi; i++) {  // insertion by the exact key
       const uint32_t v = perm[i];
@@ -348,6 +346,10 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
   uint32_t *kl = kh + cap;                              // cap
   int32_t *sidx = reinterpret_cast<int32_t *>(kl + cap);  // cap
   uint32_t *hist = reinterpret_cast<uint32_t *>(sidx + cap);  // HBINS
+  // the bucket sort's permutation: the histogram's second half, or its own cap entries
+  const bool own_perm = cap > HBINS / 2;
+  uint32_t *perm = own_perm ? hist + HBINS : hist + HBINS / 2;
+  const int nb = own_perm ? HBINS : HBINS / 2;
   __shared__ double xs[kMaxP];
   __shared__ float xf[kMaxP];
   __shared__ uint32_t warp_tmp[32];
@@ -409,7 +411,8 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     if (cnt > cap || cnt < M)  // too many ties at the boundary (or, defensively, too few)
       cnt = knn_exact_location(X, N, p, M, xs, kh, kl, sidx, hist, cap, warp_tmp, &sh_bin,
                                &sh_below, &sh_count, pref);
-    if (!bucket_order(kh, kl, sidx, cnt, M, hist, warp_tmp, &sh_count, &sh_dmax, out)) {
+    if (cnt > cap || !bucket_order(kh, kl, sidx, cnt, M, hist, nb, perm, warp_tmp, &sh_count,
+                                   &sh_dmax, out)) {
       int n2 = 1;
       while (n2 < cnt) n2 <<= 1;
       for (int i = cnt + threadIdx.x; i < n2; i += KB) {
@@ -431,7 +434,9 @@ int knn_cap(int M) {
   return cap;
 }
 
-size_t knn_smem_bytes(int cap) { return (size_t)cap * (4 + 4 + 4) + HBINS * 4; }
+size_t knn_smem_bytes(int cap) {
+  return (size_t)cap * (4 + 4 + 4) + HBINS * 4 + (cap > HBINS / 2 ? (size_t)cap * 4 : 0);
+}
 
 int knn_grid(int64_t T, int num_sms, size_t smem) {
   int per_sm = (int)(200000 / (smem + 1024));  // leave room, at most 8 CTAs of 256 threads
