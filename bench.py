@@ -82,6 +82,19 @@ def mixed_fp32_ops_per_location(n0, n, M, p):
     return float(total)
 
 
+def mspe_mixed_fp32_ops_per_location(n0, n, M, p):
+    """FP32 operations of the float-float MSPE screen for one location: every pool
+    candidate at step j costs 36j + 18 (three compensated row dots, u_s.u_c, u_s.ud_c and
+    q_j.u_c) + 20p + 3 (squared distance) + 11 (scaling by 1/theta) + 66 (exponential) + 14
+    (Kd(s, c)) + 18 (two new row entries) + 42 (v and cov) + 75 (the four derivative sums)
+    + 170 (J(c): four float-float divisions, eight products, six sums) + 6 (tracking)."""
+    total = 0
+    for j in range(n - 1):
+        pool = M - (j + 1)
+        total += pool * (36 * j + 18 + 20 * p + 3 + 11 + 66 + 14 + 18 + 42 + 75 + 170 + 6)
+    return float(total)
+
+
 def factor_stream_bytes_per_location(n, M):
     """Bytes of candidate factor rows the screen reads for one location: every pool
     candidate at step j reads its j float-float entries (8 bytes each)."""
@@ -113,19 +126,20 @@ def _workloads():
     return {
         "paper-2d": dict(make=inputs.paper_2d, variants=[("alc", "fp64"), ("alc", "mixed")],
                          head=("alc", "mixed"), cpu=1600, paper=None),
-        "smooth-8d": dict(make=inputs.smooth_8d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64")],
+        "smooth-8d": dict(make=inputs.smooth_8d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
+                                                            ("mspe", "mixed")],
                           head=("alc", "mixed"), cpu=120, paper=None),
-        "grid-2d": dict(make=inputs.grid_2d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("nn", "fp64")],
+        "grid-2d": dict(make=inputs.grid_2d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("mspe", "mixed"), ("nn", "fp64")],
                         head=("alc", "mixed"), cpu=1600,
                         paper={"value": 10000 / 30.0, "what": "Sec. 4.1: about 30 s for 10K locations, "
                                "40K-point 2-d design, ALC, n=50, fixed theta, 8 threads on a 4-core iMac"}),
         "borehole": dict(make=lambda: inputs.borehole(4000, 500),
-                         variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("nn", "fp64")],
+                         variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("mspe", "mixed"), ("nn", "fp64")],
                          head=("alc", "mixed"), cpu=500,
                          paper={"value": 500 / 23.2, "what": "Table 1 alc.nomle: 23.2 s for 500 locations "
                                 "(fit + predict), N=4000, n=50, 8 threads on a 4-core iMac"}),
         "borehole-8000": dict(make=lambda: inputs.borehole(8000, 1000),
-                              variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("nn", "fp64")],
+                              variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("mspe", "mixed"), ("nn", "fp64")],
                               head=("alc", "mixed"), cpu=1000,
                               paper={"value": 1000 / 45.1, "what": "Table SM.1 alc.nomle: 45.1 s for 1000 "
                                      "locations (fit + predict), N=8000, n=50, 8 threads on a 4-core iMac"}),
@@ -330,6 +344,17 @@ def roofline_for(prec, w, sel_ms, traffic, method="alc"):
     T, M = w.T, w.ncand
     if method == "nn":
         return None  # no scoring: kernels (b)+(c) only evaluate the predictive equations
+    if method == "mspe" and prec == "mixed":
+        work = mspe_mixed_fp32_ops_per_location(w.n0, w.n, M, w.p)
+        achieved = work * T / (sel_ms / 1e3) / 1e12
+        return {"kernel": "select_mspe_mixed_kernel (kernels b+c)", "bound": "alu",
+                "achieved": achieved, "peak": FP32_PEAK_TOPS_DERIVED, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TOPS_DERIVED, "traffic": traffic,
+                "peak_source": "derived FP32: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane-cycle)",
+                "work_per_location": work,
+                "work_unit": "FP32 operations of the float-float screen (add, mul or FMA = 1)",
+                "factor_stream_tbs": 2 * factor_stream_bytes_per_location(w.n, M) * T / (sel_ms / 1e3) / 1e12,
+                "factor_stream_note": "bytes of the two factor-row arrays read per second, kernels (b)+(c) time"}
     if method == "mspe":
         work = mspe_flops_per_location(w.n0, w.n, M, w.p)
         achieved = work * T / (sel_ms / 1e3) / 1e12

@@ -66,10 +66,11 @@ extern "C" {
 typedef enum { LAGP_ALC = 0, LAGP_MSPE = 1, LAGP_NN = 2 } lagp_method;
 
 /* LAGP_FP64: every step in FP64.
- * LAGP_MIXED: the ALC candidate screen runs in float-float (pairs of FP32, about 48
- * significant bits) on the FP32 pipes; near-tied decisions are re-scored in FP64 and the
- * predictive equations are evaluated in FP64 on the final design.  MSPE runs in FP64 only
- * (LAGP_MIXED with LAGP_MSPE returns LAGP_ERR_UNSUPPORTED); NN has no screen. */
+ * LAGP_MIXED: the candidate screen (ALC or MSPE) runs in float-float (pairs of FP32,
+ * about 48 significant bits) on the FP32 pipes; near-tied decisions, and MSPE scores whose
+ * G or J is a cancellation beyond the screen's resolution, are re-scored in FP64.  The MSPE
+ * design bookkeeping (inverse factor, F_j, dmu_j(x)) stays FP64, and the predictive
+ * equations are evaluated in FP64 on the final design.  NN has no screen. */
 typedef enum { LAGP_FP64 = 0, LAGP_MIXED = 1 } lagp_precision;
 
 /* Human-readable name of a return code; never NULL, static storage. */

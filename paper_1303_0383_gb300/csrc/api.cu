@@ -63,7 +63,8 @@ int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t
 }
 
 int check_supported(int32_t method, int32_t precision) {
-  if (method == LAGP_MSPE && precision != LAGP_FP64) return LAGP_ERR_UNSUPPORTED;
+  (void)method;
+  (void)precision;
   return LAGP_OK;
 }
 

@@ -322,6 +322,7 @@ extern "C" int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t n
       st = select_prepare();
       if (!st) st = select_mixed_prepare();
       if (!st) st = select_mspe_prepare();
+      if (!st) st = select_mspe_mixed_prepare();
       if (st) return st;
       cudaStream_t cap = capture_stream(di.device);
       if (!cap) return LAGP_ERR_CUDA;

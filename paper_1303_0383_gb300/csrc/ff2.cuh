@@ -60,6 +60,22 @@ __device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
   return fast_two_sum2(sub2(f2s(0.0f), np), e);
 }
 
+// a / b: the FP32 quotient q1 = a_h / b_h (through the reciprocal), the remainder
+// a - b q1 formed with TwoProd of b_h q1, and one correction q2 = remainder / b_h.
+__device__ __forceinline__ ff2 ff2_div(ff2 a, ff2 b) {
+  const float2 rb = f2(__frcp_rn(b.h.x), __frcp_rn(b.h.y));
+  const float2 q1 = mul2(a.h, rb);
+  const float2 np = mul2(neg2(b.h), q1);           // -p, p = rn(b_h q1)
+  float2 e = fma2(b.h, q1, np);                    // b_h q1 - p, exact
+  e = fma2(b.l, q1, e);                            // b q1 - p to FP32 accuracy
+  const float2 r = add2(sub2(add2(a.h, np), e), a.l);
+  return fast_two_sum2(q1, mul2(r, rb));
+}
+
+__device__ __forceinline__ ff2 ff2_bcast(ff a) { return ff2{f2s(a.h), f2s(a.l)}; }
+// exact scaling by a power of two
+__device__ __forceinline__ ff2 ff2_scale(ff2 a, float s) { return ff2{mul2(a.h, f2s(s)), mul2(a.l, f2s(s))}; }
+
 // Compensated accumulation of acc - sum_i a_i b_i for float-float a_i (the same for both
 // lanes) and pairs b_i: the running sum h is plain FP32; the rounding error of every
 // addition (TwoSum, exact) and of every product (TwoProd with the cross terms a_h b_l and

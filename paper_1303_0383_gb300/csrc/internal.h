@@ -112,6 +112,10 @@ int mle_prepare();
 // MSPE variant of kernels (b)+(c), FP64.
 size_t select_mspe_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
 int select_mspe_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+// MSPE, mixed precision: float-float screen, FP64 bookkeeping and decisions.
+size_t select_mspe_mixed_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
+int select_mspe_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+#define LAGP_MSPE_MIX_CTAS_PER_SM 2  // resident CTAs per SM of the mixed MSPE kernel
 
 // Batched launch of kernels (b)+(c): per-location tables in device memory (batch.cuh),
 // one persistent launch of G = ctas_per_sm x SMs CTAs over the cost-ordered queue.
@@ -137,12 +141,16 @@ int select_max_ctas(int32_t method, int32_t precision);
 int select_prepare();
 int select_mixed_prepare();
 int select_mspe_prepare();
+int select_mspe_mixed_prepare();
 size_t select_batch_workspace_bytes(const BatchLaunch &b, int num_sms);
 int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStream_t stream);
 size_t select_mixed_batch_workspace_bytes(const BatchLaunch &b, int G);
 int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G, cudaStream_t stream);
 size_t select_mspe_batch_workspace_bytes(const BatchLaunch &b, int G);
 int select_mspe_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G, cudaStream_t stream);
+size_t select_mspe_mixed_batch_workspace_bytes(const BatchLaunch &b, int G);
+int select_mspe_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, int G,
+                                   cudaStream_t stream);
 
 // Argument checks shared by the entry points (api.cu).
 int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,

@@ -262,7 +262,9 @@ size_t sel_smem_bytes(int Mpad, int n) {
 
 size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
                               int32_t precision, int num_sms) {
-  if (method == LAGP_MSPE) return select_mspe_workspace_bytes(T, p, n, ncand, num_sms);
+  if (method == LAGP_MSPE)
+    return precision == LAGP_MIXED ? select_mspe_mixed_workspace_bytes(T, p, n, ncand, num_sms)
+                                   : select_mspe_workspace_bytes(T, p, n, ncand, num_sms);
   if (precision == LAGP_MIXED && method == LAGP_ALC)
     return select_mixed_workspace_bytes(T, p, n, ncand, num_sms);
   const size_t Mpad = (size_t)mpad_of(ncand);
@@ -273,7 +275,9 @@ size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, in
 
 int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream) {
   if (a.T == 0) return LAGP_OK;
-  if (a.method == LAGP_MSPE) return select_mspe_launch(a, ws, ws_bytes, stream);
+  if (a.method == LAGP_MSPE)
+    return a.precision == LAGP_MIXED ? select_mspe_mixed_launch(a, ws, ws_bytes, stream)
+                                     : select_mspe_launch(a, ws, ws_bytes, stream);
   if (a.precision == LAGP_MIXED && a.method == LAGP_ALC)
     return select_mixed_launch(a, ws, ws_bytes, stream);
   DevInfo di;
@@ -359,7 +363,7 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
 }
 
 int select_max_ctas(int32_t method, int32_t precision) {
-  if (method == LAGP_MSPE) return 1;
+  if (method == LAGP_MSPE) return precision == LAGP_MIXED ? LAGP_MSPE_MIX_CTAS_PER_SM : 1;
   if (precision == LAGP_MIXED && method == LAGP_ALC) return LAGP_MIX_CTAS_PER_SM;
   return 2;
 }
@@ -374,7 +378,9 @@ static int batch_grid(const BatchLaunch &b, int num_sms) {
 
 size_t select_batch_workspace_bytes(const BatchLaunch &b, int num_sms) {
   const int G = batch_grid(b, num_sms);
-  if (b.method == LAGP_MSPE) return select_mspe_batch_workspace_bytes(b, G);
+  if (b.method == LAGP_MSPE)
+    return b.precision == LAGP_MIXED ? select_mspe_mixed_batch_workspace_bytes(b, G)
+                                     : select_mspe_batch_workspace_bytes(b, G);
   if (b.precision == LAGP_MIXED && b.method == LAGP_ALC) return select_mixed_batch_workspace_bytes(b, G);
   return select_scratch_bytes_for_grid(G, b.pmax, b.nmax, b.Mmax);
 }
@@ -387,7 +393,9 @@ int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStr
   st = exp_table_upload();
   if (st) return st;
   const int G = batch_grid(b, di.num_sms);
-  if (b.method == LAGP_MSPE) return select_mspe_batch_launch(b, ws, ws_bytes, G, stream);
+  if (b.method == LAGP_MSPE)
+    return b.precision == LAGP_MIXED ? select_mspe_mixed_batch_launch(b, ws, ws_bytes, G, stream)
+                                     : select_mspe_batch_launch(b, ws, ws_bytes, G, stream);
   if (b.precision == LAGP_MIXED && b.method == LAGP_ALC)
     return select_mixed_batch_launch(b, ws, ws_bytes, G, stream);
   if (ws_bytes < select_scratch_bytes_for_grid(G, b.pmax, b.nmax, b.Mmax)) return LAGP_ERR_INVALID_ARG;

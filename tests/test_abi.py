@@ -93,7 +93,8 @@ def test_batch_arguments_are_checked_on_the_host():
     assert call([0, 1], [10, 10], [50, 501]) == lagp.LAGP_ERR_INVALID_ARG    # ncand > N
     assert call([0, 1], [10, 300], [50, 400]) == lagp.LAGP_ERR_INVALID_ARG   # n > 256
     assert call([0, 1], [10, 10], [50, 40], ldxx=4) == lagp.LAGP_ERR_INVALID_ARG  # ldxx < p
-    assert call([0, 1], [10, 10], [50, 40], method=1, precision=1) == lagp.LAGP_ERR_UNSUPPORTED
+    assert call([0, 1], [10, 10], [50, 40], method=3) == lagp.LAGP_ERR_INVALID_ARG  # method
+    assert call([0, 1], [10, 10], [50, 40], precision=2) == lagp.LAGP_ERR_INVALID_ARG  # precision
 
 
 def test_server_arguments_are_checked_on_the_host():

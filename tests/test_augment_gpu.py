@@ -30,7 +30,8 @@ def gpu_augment(w, cand, start, method="alc", precision="fp64", n=None):
     return r
 
 
-@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64")])
+@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
+                                              ("mspe", "mixed")])
 def test_augmenting_a_prefix_reproduces_the_design(method, precision):
     w = inputs.tiny_2d()
     full = gpu_predict(w, method, precision)
@@ -42,7 +43,8 @@ def test_augmenting_a_prefix_reproduces_the_design(method, precision):
         assert np.array_equal(a["mean"], full["mean"]) and np.array_equal(a["s2"], full["s2"]), n1
 
 
-@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64")])
+@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
+                                              ("mspe", "mixed")])
 def test_augmenting_a_design_chosen_at_another_lengthscale(method, precision):
     # saved designs of 20 points chosen at theta = 0.25, grown to 50 at theta = 0.5
     w = inputs.tiny_2d()

@@ -73,7 +73,7 @@ def uniform_one(designs, w, x, n, M, method, precision):
 
 
 @pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
-                                              ("nn", "fp64")])
+                                              ("mspe", "mixed"), ("nn", "fp64")])
 def test_batch_equals_uniform_calls_bitwise(method, precision):
     ws, design_of, n, M, XX = make_batch(seed=10, T=45)
     res, designs, _, _, _ = run_batch(ws, design_of, n, M, XX, method, precision)

@@ -35,7 +35,7 @@ def test_knn_bit_exact_borehole():
 
 
 @pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
-                                              ("nn", "fp64")])
+                                              ("mspe", "mixed"), ("nn", "fp64")])
 def test_borehole_sampled(method, precision):
     w = inputs.borehole()
     locs = np.random.default_rng(7).choice(w.T, size=16, replace=False)

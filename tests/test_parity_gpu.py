@@ -249,16 +249,44 @@ def test_mspe_parity_smooth_8d_sample():
     assert not bad, bad[:3]
 
 
-def test_mspe_mixed_is_refused():
-    torch = _torch()
-    w = inputs.random_case(9, 300, 2, 4, 4, 15, 40)
-    X, Z, XX = dev(w.X, torch.float64), dev(w.Z, torch.float64), dev(w.XX, torch.float64)
-    with pytest.raises(lagp.LagpError) as e:
-        lagp.predict_torch(X, Z, XX, w.n0, w.n, w.ncand, w.d, w.g, "mspe", "mixed")
-    assert e.value.code == lagp.LAGP_ERR_UNSUPPORTED
+# ----------------------------------------------------------------- MSPE (mixed)
+
+def test_mspe_mixed_parity_tiny_2d():
+    w = inputs.tiny_2d()
+    g, infos, bad = run_parity(w, method="mspe", precision="mixed")
+    assert not bad, bad[:3]
 
 
-@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64")])
+@pytest.mark.parametrize("p,seed,g", [(1, 11, 1e-4), (2, 12, 1e-6), (3, 13, 1e-4), (8, 14, 1e-4)])
+def test_mspe_mixed_parity_random_small(p, seed, g):
+    w = inputs.random_case(200 + seed, 300, p, 19, 4, 18, 60, d=0.25 * p, g=g)
+    g_, infos, bad = run_parity(w, method="mspe", precision="mixed")
+    assert not bad, bad[:3]
+
+
+def test_mspe_mixed_edge_cases():
+    # n0 = n (no greedy step), ncand = n, and the smallest admissible n0
+    for w in (inputs.random_case(7, 200, 2, 9, 12, 12, 12), inputs.random_case(8, 200, 2, 9, 3, 12, 12),
+              inputs.random_case(9, 300, 2, 1, 3, 15, 40)):
+        g, infos, bad = run_parity(w, method="mspe", precision="mixed")
+        assert not bad, bad[:3]
+
+
+def test_mspe_mixed_agrees_with_fp64():
+    # the 8-d workload's shape on a sample: the two precisions choose the same designs except
+    # where a step is a near-tie within FP64 rounding, and kernel (c) gives the same values
+    w = inputs.smooth_8d(T=64)
+    f = gpu_predict(w, "mspe", "fp64")
+    m = gpu_predict(w, "mspe", "mixed")
+    assert (m["status"] == 0).all()
+    same = (f["idx"] == m["idx"]).all(axis=1)
+    assert same.mean() >= 0.95, same.mean()
+    rel = np.abs(f["s2"][same] - m["s2"][same]) / f["s2"][same]
+    assert rel.max() <= 1e-12, rel.max()
+
+
+@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
+                                              ("mspe", "mixed")])
 def test_smooth_8d_full_size_sampled(method, precision):
     # the 8-d workload in the benchmark's launch configuration (10000 locations, n = 100,
     # 2000 candidates); the oracle checks a seeded sample
