@@ -34,6 +34,21 @@ namespace {
 
 constexpr int XB = 256;  // threads per CTA
 #define LAGP_MSPE_MIX_MINB LAGP_MSPE_MIX_CTAS_PER_SM
+// Factor rows in flight per thread: each thread streams its own pair's rows of U and Ud
+// through a ring of RING stages in shared memory with asynchronous copies (cp.async), so
+// that RING - 1 rows of both arrays are on their way while one is consumed.  The arrays
+// exceed L2 on the large workloads and the loop is bound by the bytes in flight per SM.
+constexpr int RING = 6;
+
+__device__ __forceinline__ void cp_async16(float4 *smem_dst, const float4 *gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most RING - 1 of this thread's copy groups are pending
+__device__ __forceinline__ void cp_async_wait_ring() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(RING - 1) : "memory");
+}
 
 struct MxParams {
   const double *X, *Z;
@@ -87,6 +102,7 @@ __device__ __forceinline__ void merge_min(float o1, int orr, float o2, float &b1
 // The step's values for the screen: broadcast float-float scalars and the new rows.
 struct MStep {
   float4 *U, *Ud, *cs, *vp, *cp;
+  float4 *ring;           // this thread's ring: stage k holds U at [2k XB], Ud at [(2k+1) XB]
   const float4 *Xr;
   float *Jsc;             // per candidate: the screen's J (FP32), +inf when not scored
   unsigned char *flg;     // per candidate: 1 when the screen cannot resolve its J
@@ -104,6 +120,15 @@ struct MStep {
 // One step for one pair of candidates (2q, 2q+1).
 __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned char *used,
                                           float &b1, int &r1, float &b2, int &nf) {
+  // the first RING - 1 rows start on their way (one copy group per row, empty past row j)
+#pragma unroll
+  for (int st = 0; st < RING - 1; st++) {
+    if (st < C.j) {
+      cp_async16(C.ring + (2 * st) * XB, C.U + (size_t)st * C.Qpad + q);
+      cp_async16(C.ring + (2 * st + 1) * XB, C.Ud + (size_t)st * C.Qpad + q);
+    }
+    cp_async_commit();
+  }
   // squared distance of the pair to the new point, in float-float
   float2 dh = f2s(0.0f), dl = f2s(0.0f);
   for (int k = 0; k < C.p; k++) {
@@ -123,10 +148,18 @@ __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned 
   const ff2 kdc = ff2_mul(ff2_mul(kc, arg), C.thinv);                     // Kd(s, c)
   // K(s,c) - u_s.u_c, Kd(s,c) - u_s.ud_c and q_j.u_c (compensated, Dot2)
   ff2acc a1{kc.h, kc.l}, a2{kdc.h, kdc.l}, a3{f2s(0.0f), f2s(0.0f)};
-  const float4 *Ui = C.U + q, *Di = C.Ud + q;
-#pragma unroll 2
-  for (int i = 0; i < C.j; i++, Ui += C.Qpad, Di += C.Qpad) {
-    const float4 bu = *Ui, bd = *Di;
+  int sc = 0, sp = RING - 1;  // ring stages of rows i and i + RING - 1
+  for (int i = 0; i < C.j; i++) {
+    const int ip = i + RING - 1;
+    if (ip < C.j) {  // refill the stage consumed at row i - 1
+      cp_async16(C.ring + (2 * sp) * XB, C.U + (size_t)ip * C.Qpad + q);
+      cp_async16(C.ring + (2 * sp + 1) * XB, C.Ud + (size_t)ip * C.Qpad + q);
+    }
+    cp_async_commit();
+    cp_async_wait_ring();  // row i has landed
+    const float4 bu = C.ring[(2 * sc) * XB], bd = C.ring[(2 * sc + 1) * XB];
+    sc = (sc == RING - 1) ? 0 : sc + 1;
+    sp = (sp == RING - 1) ? 0 : sp + 1;
     const float4 sa = C.sr4[i], qa = C.qr4[i];
     const float2 sl = C.sr2[i], ql = C.qr2[i];
     ff2acc_sub_prod(a1, sa, sl, bu);
@@ -368,6 +401,7 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
   int *rlist = dr + ((nn + 3) & ~3);                // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   unsigned char *flg = used + Mpad;                                             // Mpad
+  float4 *ring = reinterpret_cast<float4 *>(flg + Mpad) + threadIdx.x;  // RING x 2 x XB
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
   __shared__ double xs[kMaxP], xl[kMaxP];
@@ -641,7 +675,8 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
       const double dj = (double)(jn - 2);
       const double psi = sh_psi, F = sh_d[4], dmux = sh_d[5], wKdw = sh_d[6];
       MStep C;
-      C.U = U; C.Ud = Ud; C.cs = cs; C.vp = vp; C.cp = cp; C.Xr = Xr; C.Jsc = Jsc; C.flg = flg;
+      C.U = U; C.Ud = Ud; C.cs = cs; C.vp = vp; C.cp = cp; C.ring = ring; C.Xr = Xr; C.Jsc = Jsc;
+      C.flg = flg;
       C.sr4 = sr4; C.qr4 = qr4; C.sr2 = sr2; C.qr2 = qr2; C.sxs = sxs; C.tabh = tabh; C.tabl = tabl;
       C.inv = ff2_bcast(ff_from_double(inv));
       C.uxj = ff2_bcast(ff_from_double(sh_d[1]));
@@ -709,7 +744,8 @@ size_t mxm_smem_bytes(int Mpad, int n) {
   const size_t nrow = (size_t)((n + 1) & ~1);
   return Qpad * 2 * sizeof(float4) + nrow * 2 * (sizeof(float4) + sizeof(float2)) +
          (size_t)n * 10 * sizeof(double) + (size_t)Mpad * sizeof(float) +
-         (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + 2 * (size_t)Mpad;
+         (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + 2 * (size_t)Mpad +
+         (size_t)RING * 2 * XB * sizeof(float4);
 }
 
 int mxm_grid(int64_t T, int num_sms) {
