@@ -34,6 +34,11 @@ namespace {
 constexpr int KB = 256;               // threads per CTA
 constexpr int HBITS = 12;
 constexpr int HBINS = 1 << HBITS;     // 4096 histogram bins
+// The bucket sort's permutation gets cap entries of its own where they fit in shared
+// memory next to the keys (cap <= 8192); otherwise it uses the histogram's second half
+// (HBINS / 2 entries) and larger survivor sets take the bitonic sort.
+__host__ __device__ constexpr bool knn_own_perm(int cap) { return cap > HBINS / 2 && cap <= 8192; }
+
 
 __device__ __forceinline__ double sqdist_exact(const double *x, const double *xi, int p) {
   double acc = 0.0;
@@ -347,9 +352,10 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
   int32_t *sidx = reinterpret_cast<int32_t *>(kl + cap);  // cap
   uint32_t *hist = reinterpret_cast<uint32_t *>(sidx + cap);  // HBINS
   // the bucket sort's permutation: the histogram's second half, or its own cap entries
-  const bool own_perm = cap > HBINS / 2;
+  const bool own_perm = knn_own_perm(cap);
   uint32_t *perm = own_perm ? hist + HBINS : hist + HBINS / 2;
   const int nb = own_perm ? HBINS : HBINS / 2;
+  const int perm_cap = own_perm ? cap : HBINS / 2;
   __shared__ double xs[kMaxP];
   __shared__ float xf[kMaxP];
   __shared__ uint32_t warp_tmp[32];
@@ -411,7 +417,8 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     if (cnt > cap || cnt < M)  // too many ties at the boundary (or, defensively, too few)
       cnt = knn_exact_location(X, N, p, M, xs, kh, kl, sidx, hist, cap, warp_tmp, &sh_bin,
                                &sh_below, &sh_count, pref);
-    if (cnt > cap || !bucket_order(kh, kl, sidx, cnt, M, hist, nb, perm, warp_tmp, &sh_count,
+    if (cnt > cap || cnt > perm_cap ||
+        !bucket_order(kh, kl, sidx, cnt, M, hist, nb, perm, warp_tmp, &sh_count,
                                    &sh_dmax, out)) {
       int n2 = 1;
       while (n2 < cnt) n2 <<= 1;
@@ -435,7 +442,7 @@ int knn_cap(int M) {
 }
 
 size_t knn_smem_bytes(int cap) {
-  return (size_t)cap * (4 + 4 + 4) + HBINS * 4 + (cap > HBINS / 2 ? (size_t)cap * 4 : 0);
+  return (size_t)cap * (4 + 4 + 4) + HBINS * 4 + (knn_own_perm(cap) ? (size_t)cap * 4 : 0);
 }
 
 int knn_grid(int64_t T, int num_sms, size_t smem) {

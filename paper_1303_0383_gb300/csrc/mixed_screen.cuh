@@ -126,7 +126,21 @@ __device__ __forceinline__ double corr64(const double *a, const double *b, int p
   return exp_nonpos(-acc * theta_inv, etab);
 }
 
-// One step of the screen for NP candidate pairs of this thread (Sec. 3.2 update, in
+// Asynchronous 16-byte copies global -> shared (cp.async, L2 only) and their groups: a
+// thread's factor rows in global memory reach its own slots of a ring in shared memory a
+// few rows ahead of their use, so that the loads of the next rows are in flight while a
+// row is consumed.  Each thread waits only for its own copies (no barrier).
+constexpr int RING_A = 4;  // stages per thread, where the ring is used
+
+__device__ __forceinline__ void cp_async16(float4 *smem_dst, const float4 *gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One step of the screen for one candidate pair of this thread (Sec. 3.2 update, in
 // float-float): K(s, c) from the squared distance, the new factor entry
 // u_c[j] = (K(s, c) - u_s . u_c) / L_jj, then v_{j+1}(c) = v_j(c) - u_c[j]^2,
 // cov_{j+1}(x, c) = cov_j(x, c) - u_x[j] u_c[j], and the ALC screen score cov^2 / v.
@@ -134,6 +148,7 @@ struct StepCtx {
   float4 *U;     // factor rows in global memory (rows R .. n-1 are used)
   float4 *Us;    // the first R rows, in shared memory
   int R;
+  float4 *ring;  // this thread's ring slots: stage k at ring[k * blockDim.x]
   const float4 *Xr;
   float4 *vp, *cp;
   const float4 *srow4;
@@ -145,76 +160,75 @@ struct StepCtx {
   bool want;
 };
 
-template <int NP>
-__device__ __forceinline__ void screen_pairs(const StepCtx &C, const int (&qs)[NP],
-                                             const unsigned char *used, float &b1, int &r1,
-                                             float &b2) {
-  ff2acc acc[NP];
+// RA = 0: the global rows are loaded straight into registers (four in flight); RA > 0:
+// they stream through a ring of RA stages.  The ring pays where the rows come from DRAM
+// (large n x M); where they mostly hit L2 its bookkeeping costs more than it hides.
+template <int RA>
+__device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsigned char *used,
+                                            float &b1, int &r1, float &b2) {
+  const int nt = blockDim.x;
+  const int jr = C.j < C.R ? C.j : C.R;  // rows R .. j-1 come from global memory
+  // the first RA - 1 global rows start on their way (one copy group each)
 #pragma unroll
-  for (int h = 0; h < NP; h++) {
-    const int q = qs[h];
-    // squared distance of the pair to the new point
-    float2 dh = f2s(0.0f), dl = f2s(0.0f);
-    for (int k = 0; k < C.p; k++) {
-      const ff2 b = ff2_load(C.Xr + k * C.Qpad + q);
-      const float2 a = C.sxs[k];
-      const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
-      const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
-      const float2 ph = mul2(df.h, df.h);
-      const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
-      const ff2 sacc = two_sum2(dh, ph);
-      dh = sacc.h;
-      dl = add2(add2(sacc.l, dl), pl);
-    }
-    const ff2 d2 = fast_two_sum2(dh, dl);
-    const ff2 arg = ff2_mul(d2, C.thinv2);
-    const ff2 kc = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, C.tabh, C.tabl);   // K(s, c)
-    acc[h] = ff2acc{kc.h, kc.l};
+  for (int st = 0; st < RA - 1; st++) {
+    if (jr + st < C.j) cp_async16(C.ring + st * nt, C.U + (size_t)(jr + st) * C.Qpad + q);
+    cp_async_commit();
   }
+  // squared distance of the pair to the new point
+  float2 dh = f2s(0.0f), dl = f2s(0.0f);
+  for (int k = 0; k < C.p; k++) {
+    const ff2 b = ff2_load(C.Xr + k * C.Qpad + q);
+    const float2 a = C.sxs[k];
+    const ff2 df = two_sum2(f2s(a.x), neg2(b.h));
+    const float2 dfl = add2(df.l, sub2(f2s(a.y), b.l));
+    const float2 ph = mul2(df.h, df.h);
+    const float2 pl = fma2(add2(df.h, df.h), dfl, fma2(df.h, df.h, neg2(ph)));
+    const ff2 sacc = two_sum2(dh, ph);
+    dh = sacc.h;
+    dl = add2(add2(sacc.l, dl), pl);
+  }
+  const ff2 d2 = fast_two_sum2(dh, dl);
+  const ff2 arg = ff2_mul(d2, C.thinv2);
+  const ff2 kc = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, C.tabh, C.tabl);   // K(s, c)
+  ff2acc acc{kc.h, kc.l};
   // K(s, c) - sum_i u_s[i] u_c[i]: compensated accumulation over the rows held in shared
-  // memory, then over those in global memory (four loads of U in flight either way)
-  constexpr int UNR = 4 / NP;
-  const int jr = C.j < C.R ? C.j : C.R;
-#pragma unroll UNR
-  for (int i = 0; i < jr; i++) {
-    const float4 a = C.srow4[i];
-    const float2 al = C.srow2[i];
-    float4 b[NP];
-#pragma unroll
-    for (int h = 0; h < NP; h++) b[h] = C.Us[(size_t)i * C.Qpad + qs[h]];
-#pragma unroll
-    for (int h = 0; h < NP; h++) ff2acc_sub_prod(acc[h], a, al, b[h]);
-  }
-#pragma unroll UNR
-  for (int i = jr; i < C.j; i++) {
-    const float4 a = C.srow4[i];
-    const float2 al = C.srow2[i];
-    float4 b[NP];
-#pragma unroll
-    for (int h = 0; h < NP; h++) b[h] = C.U[(size_t)i * C.Qpad + qs[h]];
-#pragma unroll
-    for (int h = 0; h < NP; h++) ff2acc_sub_prod(acc[h], a, al, b[h]);
-  }
-#pragma unroll
-  for (int h = 0; h < NP; h++) {
-    const int q = qs[h];
-    const bool u0 = used[2 * q], u1 = used[2 * q + 1];
-    const ff2 u = ff2_mul(ff2acc_result(acc[h]), C.inv2);           // u_c[j]
-    ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
-    const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
-    ff2 v = ff2_sub(v0, ff2_mul(u, u));
-    ff2 cx = ff2_sub(c0, ff2_mul(C.uxj2, u));
-    // A used lane keeps its values: the step's pivot may be the partner of a live
-    // candidate, and other threads read the pivot's v and cov at the start of the step
-    // without a barrier after it.
-    if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
-    if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
-    ff2_store(C.vp + q, v);
-    ff2_store(C.cp + q, cx);
-    if (C.want) {
-      if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), C.c0 + 2 * q, b1, r1, b2);
-      if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), C.c0 + 2 * q + 1, b1, r1, b2);
+  // memory, then over those streamed through the ring
+#pragma unroll 4
+  for (int i = 0; i < jr; i++)
+    ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], C.Us[(size_t)i * C.Qpad + q]);
+  if constexpr (RA == 0) {
+#pragma unroll 4
+    for (int i = jr; i < C.j; i++)
+      ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], C.U[(size_t)i * C.Qpad + q]);
+  } else {
+    int sc = 0, sp = RA - 1;  // ring stages of rows i and i + RA - 1
+    for (int i = jr; i < C.j; i++) {
+      const int ip = i + RA - 1;
+      if (ip < C.j) cp_async16(C.ring + sp * nt, C.U + (size_t)ip * C.Qpad + q);
+      cp_async_commit();
+      cp_async_wait<RA - 1>();  // row i has landed
+      const float4 b = C.ring[sc * nt];
+      sc = (sc == RA - 1) ? 0 : sc + 1;
+      sp = (sp == RA - 1) ? 0 : sp + 1;
+      ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], b);
     }
+  }
+  const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+  const ff2 u = ff2_mul(ff2acc_result(acc), C.inv2);               // u_c[j]
+  ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
+  const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
+  ff2 v = ff2_sub(v0, ff2_mul(u, u));
+  ff2 cx = ff2_sub(c0, ff2_mul(C.uxj2, u));
+  // A used lane keeps its values: the step's pivot may be the partner of a live
+  // candidate, and other threads read the pivot's v and cov at the start of the step
+  // without a barrier after it.
+  if (u0) { v.h.x = v0.h.x; v.l.x = v0.l.x; cx.h.x = c0.h.x; cx.l.x = c0.l.x; }
+  if (u1) { v.h.y = v0.h.y; v.l.y = v0.l.y; cx.h.y = c0.h.y; cx.l.y = c0.l.y; }
+  ff2_store(C.vp + q, v);
+  ff2_store(C.cp + q, cx);
+  if (C.want) {
+    if (!u0 && v.h.x > 0.0f) track2(__fdiv_rn(cx.h.x * cx.h.x, v.h.x), C.c0 + 2 * q, b1, r1, b2);
+    if (!u1 && v.h.y > 0.0f) track2(__fdiv_rn(cx.h.y * cx.h.y, v.h.y), C.c0 + 2 * q + 1, b1, r1, b2);
   }
 }
 

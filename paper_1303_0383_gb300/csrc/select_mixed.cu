@@ -59,6 +59,7 @@ struct MixParams {
 #ifndef LAGP_MIX_MINB
 #define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM, each with its first factor rows in shared memory
 #endif
+template <int RA>
 __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, nmax = P.nmax;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   float4 *Us = reinterpret_cast<float4 *>(used + P.Mpad);    // R x Qpad: first factor rows
   const int R = P.R;
+  float4 *ring = Us + (size_t)R * Qpad + threadIdx.x;        // RA x MB: row ring
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
   __shared__ double xl[kMaxP];
@@ -193,13 +195,11 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       const ff2 thinv2{f2s(thinv.h), f2s(thinv.l)};
       float b1 = -1.0f, b2 = -1.0f;
       int r1 = 0x7fffffff;
-      const StepCtx C{U, Us, R, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2, thinv2, Qpad, p, j, 0, want};
-      // one pair at a time (interleaving two pairs per thread measured slower: the extra
-      // loads in flight only add L2 pressure)
+      const StepCtx C{U, Us, R, ring, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2, thinv2,
+                      Qpad, p, j, 0, want};
       for (int q = tid; q < Q; q += MB) {
         if (used[2 * q] && used[2 * q + 1]) continue;
-        const int qs[1] = {q};
-        screen_pairs<1>(C, qs, used, b1, r1, b2);
+        screen_pair<RA>(C, q, used, b1, r1, b2);
       }
       // best and second-best screen scores: warp shuffles, one barrier, then every
       // thread merges the per-warp results itself (double-buffered by step parity)
@@ -256,26 +256,47 @@ int mix_grid(int64_t T, int num_sms) {
 
 int mix_mpad(int M) { return (int)align_up((size_t)M, 64); }
 
-// Dynamic shared memory: the per-candidate state, then the first R factor rows.  Mpad is
-// a multiple of 64, so the rows start 16-byte aligned.
-size_t mix_smem_bytes(int Mpad, int n, int R) {
+
+// Dynamic shared memory: the per-candidate state, then the first R factor rows and the
+// threads' row rings (RA stages).  Mpad is a multiple of 64, so the rows start 16-byte aligned.
+size_t mix_smem_bytes(int Mpad, int n, int R, int RA) {
   const size_t Qpad = (size_t)Mpad / 2;
   const size_t nrow = (size_t)((n + 1) & ~1);
   return Qpad * 2 * sizeof(float4) +
          (size_t)(MB / 32) * (nrow * (sizeof(float4) + sizeof(float2)) + kMaxP * sizeof(float2)) +
          (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + (size_t)Mpad +
-         (size_t)R * Qpad * sizeof(float4);
+         (size_t)R * Qpad * sizeof(float4) + (size_t)RA * MB * sizeof(float4);
 }
+
+
 
 // Factor rows kept in shared memory: as many as LAGP_MIX_MINB resident CTAs per SM leave
 // room for (the rest stream from L2).  Row i is read at every step after step i, so the
 // first rows carry the most traffic.
-int mix_rows_in_smem(int Mpad, int n, const DevInfo &di) {
+size_t mix_static_smem(int RA) {
   cudaFuncAttributes fa;
-  size_t stat = 4096;
-  if (cudaFuncGetAttributes(&fa, select_mixed_kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+  const cudaError_t e = RA ? cudaFuncGetAttributes(&fa, select_mixed_kernel<RING_A>)
+                           : cudaFuncGetAttributes(&fa, select_mixed_kernel<0>);
+  return e == cudaSuccess ? fa.sharedSizeBytes : 4096;
+}
+
+// The row ring is used where a CTA's factor rows (n x M float-float entries) come mostly
+// from DRAM -- 8-d workload (n = 100, M = 2000) yes, paper-2d (n = 50, M = 1000) no, both
+// measured -- and only if its shared memory leaves as many CTAs resident per SM.
+int mix_ring_stages(int Mpad, int n, int M, const DevInfo &di) {
+  if ((int64_t)n * M < 100000) return 0;
+  auto resident = [&](int RA) {
+    const size_t per = mix_static_smem(RA) + 1024 + mix_smem_bytes(Mpad, n, 0, RA);
+    const size_t k = di.smem_per_sm / per;
+    return k < (size_t)LAGP_MIX_MINB ? k : (size_t)LAGP_MIX_MINB;
+  };
+  return resident(RING_A) >= resident(0) ? RING_A : 0;
+}
+
+int mix_rows_in_smem(int Mpad, int n, int RA, const DevInfo &di) {
+  const size_t stat = mix_static_smem(RA);
   size_t per_cta = di.smem_per_sm / LAGP_MIX_MINB;
-  const size_t fixed = stat + 1024 + mix_smem_bytes(Mpad, n, 0);  // 1 KB reserved per CTA
+  const size_t fixed = stat + 1024 + mix_smem_bytes(Mpad, n, 0, RA);  // 1 KB reserved per CTA
   if (per_cta > di.smem_optin) per_cta = di.smem_optin;
   if (per_cta <= fixed) return 0;
   const size_t row = (size_t)Mpad / 2 * sizeof(float4);
@@ -315,15 +336,21 @@ int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, ch
   // the design goes to the caller's idx, or to the workspace when the caller wants none
   P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(o);
   o += L.idx;
-  P.R = mix_rows_in_smem(P.Mpad, P.nmax, di);
-  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax, P.R);
+  const int RA = mix_ring_stages(P.Mpad, P.nmax, P.M, di);
+  P.R = mix_rows_in_smem(P.Mpad, P.nmax, RA, di);
+  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax, P.R, RA);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(select_mixed_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = RA ? cudaFuncSetAttribute(select_mixed_kernel<RING_A>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                     : cudaFuncSetAttribute(select_mixed_kernel<0>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaMemsetAsync(w, 0, 512, stream);  // work counter and re-score counter
   if (e != cudaSuccess) return cuda_status(e);
-  select_mixed_kernel<<<G, MB, smem, stream>>>(P);
+  if (RA)
+    select_mixed_kernel<RING_A><<<G, MB, smem, stream>>>(P);
+  else
+    select_mixed_kernel<0><<<G, MB, smem, stream>>>(P);
   g_launches.fetch_add(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);

@@ -38,17 +38,8 @@ constexpr int XB = 256;  // threads per CTA
 // through a ring of RING stages in shared memory with asynchronous copies (cp.async), so
 // that RING - 1 rows of both arrays are on their way while one is consumed.  The arrays
 // exceed L2 on the large workloads and the loop is bound by the bytes in flight per SM.
+// (cp_async16 and its groups: mixed_screen.cuh)
 constexpr int RING = 6;
-
-__device__ __forceinline__ void cp_async16(float4 *smem_dst, const float4 *gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most RING - 1 of this thread's copy groups are pending
-__device__ __forceinline__ void cp_async_wait_ring() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(RING - 1) : "memory");
-}
 
 struct MxParams {
   const double *X, *Z;
@@ -156,7 +147,7 @@ __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned 
       cp_async16(C.ring + (2 * sp + 1) * XB, C.Ud + (size_t)ip * C.Qpad + q);
     }
     cp_async_commit();
-    cp_async_wait_ring();  // row i has landed
+    cp_async_wait<RING - 1>();  // row i has landed
     const float4 bu = C.ring[(2 * sc) * XB], bd = C.ring[(2 * sc + 1) * XB];
     sc = (sc == RING - 1) ? 0 : sc + 1;
     sp = (sp == RING - 1) ? 0 : sp + 1;

@@ -63,7 +63,10 @@ def test_knn_bit_exact_tiny_2d():
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("p,N,T,M", [(1, 777, 13, 64), (3, 1234, 37, 97), (8, 3001, 19, 500)])
+# the last two: survivor capacities 8192 (the bucket sort's own permutation array) and
+# 16384 (the largest candidate count, 8192; permutation in the histogram or bitonic sort)
+@pytest.mark.parametrize("p,N,T,M", [(1, 777, 13, 64), (3, 1234, 37, 97), (8, 3001, 19, 500),
+                                     (2, 12000, 5, 4000), (2, 20000, 5, 8192)])
 def test_knn_bit_exact_random_ragged(p, N, T, M):
     w = inputs.random_case(11 + p, N, p, T, 3, 10, M)
     assert np.array_equal(gpu_knn(w.X, w.XX, M), oracle.knn(w.X, w.XX, M))
