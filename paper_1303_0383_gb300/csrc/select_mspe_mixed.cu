@@ -69,6 +69,45 @@ __device__ __forceinline__ bool j_better64(double a, int ra, double b, int rb) {
   return a < b || (a == b && ra < rb);
 }
 
+// The O(j^2) products of the FP64 step, y1[i] = sum_{m in [lo(i), hi(i))} A1[i][m] x1[m]
+// (and y2 likewise with A2, x2 when A2 is given), for rows i < rows of row-major matrices
+// with leading dimension nn.  Each row is split over SPLIT threads (strided entries), so
+// all warps of the CTA issue FP64 work and each chain is SPLIT times shorter; the partial
+// sums meet in `part` (shared memory) and are added in a fixed order, so the result does
+// not depend on the schedule.  Ends with the outputs written through out(i, y1, y2) and a
+// barrier.
+constexpr int SPLIT = 4;
+template <class Lo, class Hi, class Out>
+__device__ __forceinline__ void split_rows(const double *A1, const double *x1, const double *A2,
+                                           const double *x2, int nn, int rows, Lo lo, Hi hi,
+                                           double *part, Out out) {
+  const int tid = threadIdx.x;
+  for (int base = 0; base < rows; base += XB / SPLIT) {
+    const int i = base + tid / SPLIT, c = tid % SPLIT;
+    if (i < rows) {
+      const double *a1 = A1 + (size_t)i * nn, *a2 = A2 ? A2 + (size_t)i * nn : nullptr;
+      double s1 = 0.0, s2 = 0.0;
+      const int h = hi(i);
+      for (int m = lo(i) + c; m < h; m += SPLIT) {
+        s1 = fma(a1[m], x1[m], s1);
+        if (a2) s2 = fma(a2[m], x2[m], s2);
+      }
+      part[2 * tid] = s1;
+      part[2 * tid + 1] = s2;
+    }
+    __syncthreads();
+    if (tid < XB / SPLIT && base + tid < rows) {
+      double y1 = 0.0, y2 = 0.0;
+      for (int k = 0; k < SPLIT; k++) {
+        y1 += part[2 * (tid * SPLIT + k)];
+        y2 += part[2 * (tid * SPLIT + k) + 1];
+      }
+      out(base + tid, y1, y2);
+    }
+    __syncthreads();
+  }
+}
+
 // Screen score comparison for a minimum: smaller score, ties to the smaller rank.
 __device__ __forceinline__ void track_min(float sc, int c, float &b1, int &r1, float &b2) {
   if (sc < b1 || (sc == b1 && c < r1)) {
@@ -224,7 +263,7 @@ struct MRescore {
   const double *xl, *etab;
   const unsigned char *used, *flg;
   const float *Jsc;
-  const int *dr;
+  const int *dg;                    // design indices in X
   const double *LiT, *Qf;           // FP64 inverse factor (transposed) and Q (full)
   const double *ux, *yt, *r;        // u_x, ytil and Q ytil of the design
   double *wk;                       // this warp's scratch: k, kd, u, ud (nn each)
@@ -232,7 +271,7 @@ struct MRescore {
   double *red_s;
   int *red_r;
   int p, M, jd, nn;
-  double theta_inv, th2, onepg, psi, vx, F, dmux, wKdw;
+  double theta_inv, ith2, onepg, psi, vx, F, dmux, wKdw;
 };
 
 // Candidates within 2 DELTA of the screen's best (or flagged) are re-scored; returns (to
@@ -262,7 +301,7 @@ __device__ int mspe_rescore(const MRescore &R, float B1) {
     if (R.used[c]) continue;
     const double *xc = R.X + (int64_t)R.cnd[c] * p;
     for (int i = lane; i < jd; i += 32) {
-      const double *xi = R.X + (int64_t)R.cnd[R.dr[i]] * p;
+      const double *xi = R.X + (int64_t)R.dg[i] * p;
       double acc = 0.0;
       for (int k = 0; k < p; k++) {
         const double t = xi[k] - xc[k];
@@ -270,7 +309,7 @@ __device__ int mspe_rescore(const MRescore &R, float B1) {
       }
       const double kk = exp_nonpos(-acc * R.theta_inv, R.etab);
       wkk[i] = kk;
-      wkd[i] = kk * acc / R.th2;
+      wkd[i] = kk * acc * R.ith2;
     }
     __syncwarp();
     // u = L^{-1} k_c and ud = L^{-1} kd_c: lane-owned rows i, L^{-1}[i][m] = LiT[m][i]
@@ -389,10 +428,13 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
   double *ks = t2 + nn;         // nn: k_j(s)
   float *Jsc = reinterpret_cast<float *>(ks + nn);  // Mpad
   int *dr = reinterpret_cast<int *>(Jsc + Mpad);    // nn (padded to 4): ranks of the design
-  int *rlist = dr + ((nn + 3) & ~3);                // RESCORE_CAP
+  int *dg = dr + ((nn + 3) & ~3);                   // nn (padded to 4): design indices in X
+  int *rlist = dg + ((nn + 3) & ~3);                // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   unsigned char *flg = used + Mpad;                                             // Mpad
   float4 *ring = reinterpret_cast<float4 *>(flg + Mpad) + threadIdx.x;  // RING x 2 x XB
+  // the FP64 step's partial sums (2 x XB doubles) reuse the ring, idle outside the screen
+  double *part = reinterpret_cast<double *>(flg + Mpad);
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
   __shared__ double xs[kMaxP], xl[kMaxP];
@@ -404,7 +446,7 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
   __shared__ double sh_d[8];  // 0 inv, 1 uxj, 2 ytj, 3 rj, 4 F, 5 dmux, 6 wKdw
   __shared__ double sh_dot[4];
   __shared__ int sh_loc, sh_fail, sh_nlist;
-  __shared__ double sh_psi, sh_vx, sh_trR, sh_nQ2, sh_yRy;
+  __shared__ double sh_psi, sh_vx, sh_trR, sh_nQ2, sh_yRy, sh_zs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < 64) {
     tabh[tid] = c_exp.tabf_h[tid];
@@ -432,6 +474,7 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
     const int n = L.n, p = L.p, M = L.M;
     const int32_t *cnd = L.cand;
     const double th = L.theta, th2 = th * th, th3 = th2 * th, th4 = th2 * th2;
+    const double ith2 = 1.0 / th2, ith3 = 1.0 / th3, ith4 = 1.0 / th4;
     const ff thinv = ff_from_double(L.theta_inv);
     const ff onepg = ff_from_double(L.onepg);
     // the start design: the n0 nearest, or a saved design (augmentation)
@@ -488,35 +531,42 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
         break;
       }
       // ---- FP64 phase A: the pivot's coordinates, k_j(s), Kd and Kdd rows, u_s = L^{-1} k_j(s)
-      if (tid < p) xs[tid] = L.X[(int64_t)cnd[s] * p + tid];
+      // the pivot's coordinates and response in one round of loads
+      if (tid <= p) {
+        const int64_t gs = cnd[s];
+        if (tid < p) xs[tid] = L.X[gs * p + tid];
+        else sh_zs = L.Z[gs];
+      }
       __syncthreads();
       for (int i = tid; i <= j; i += XB) {
         double kk = 0.0, kd = 0.0, kdd = 0.0;
         if (i < j) {
-          const double *xi = L.X + (int64_t)cnd[dr[i]] * p;
+          const double *xi = L.X + (int64_t)dg[i] * p;
           double acc = 0.0;
           for (int k = 0; k < p; k++) {
             const double t = xs[k] - xi[k];
             acc = fma(t, t, acc);
           }
           kk = exp_nonpos(-acc * L.theta_inv, etab);
-          kd = kk * acc / th2;
-          kdd = kk * (acc * acc / th4 - 2.0 * acc / th3);
+          kd = kk * acc * ith2;
+          kdd = kk * (acc * acc * ith4 - 2.0 * acc * ith3);
           ks[i] = kk;
         }
+        // Kd and Kdd are kept symmetric in full, so that every product reads rows
         Kd[(size_t)j * nn + i] = kd;
         Kdd[(size_t)j * nn + i] = kdd;
+        Kd[(size_t)i * nn + j] = kd;
+        Kdd[(size_t)i * nn + j] = kdd;
       }
       __syncthreads();
-      for (int i = tid; i < j; i += XB) {
-        double acc = 0.0;
-        for (int m = 0; m <= i; m++) acc = fma(LiT[(size_t)m * nn + i], ks[m], acc);
-        srow[i] = acc;
-        const ff f = ff_from_double(acc);
-        sr4[i] = make_float4(f.h, f.h, -f.h, -f.h);
-        sr2[i] = f2s(f.l);
-      }
-      __syncthreads();
+      // u_s[i] = sum_{m <= i} L^{-1}[i][m] k_j(s)[m]
+      split_rows(Li, ks, nullptr, nullptr, nn, j, [](int) { return 0; },
+                 [](int i) { return i + 1; }, part, [&](int i, double v, double) {
+                   srow[i] = v;
+                   const ff f = ff_from_double(v);
+                   sr4[i] = make_float4(f.h, f.h, -f.h, -f.h);
+                   sr2[i] = f2s(f.l);
+                 });
       // u_s.u_s, u_s.u_x, u_s.ytil, u_s.udx: one warp each
       if (warp < 4) {
         double acc = 0.0;
@@ -539,9 +589,9 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
             acc = fma(t, t, acc);
           }
           const double kxs = exp_nonpos(-acc * L.theta_inv, etab);
-          const double kdxs = kxs * acc / th2;
-          const double uxj = (kxs - sh_dot[1]) / sq;
-          const double ytj = (L.Z[cnd[s]] - sh_dot[2]) / sq;
+          const double kdxs = kxs * acc * ith2;
+          const double uxj = (kxs - sh_dot[1]) * inv;
+          const double ytj = (sh_zs - sh_dot[2]) * inv;
           ux[j] = uxj;
           udx[j] = (kdxs - sh_dot[3]) * inv;
           yt[j] = ytj;
@@ -551,53 +601,43 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
           sh_psi = fma(ytj, ytj, sh_psi);
           sh_vx = fma(-uxj, uxj, sh_vx);
           dr[j] = s;
+          dg[j] = cnd[s];
           used[s] = 1;
         }
       }
       __syncthreads();
       if (sh_fail) break;
       const double inv = sh_d[0];
-      // ---- FP64 phase B: row j of L^{-1} (and column j of its transpose)
-      for (int i = tid; i <= j; i += XB) {
-        double li;
-        if (i == j) {
-          li = inv;
-        } else {
-          double acc = 0.0;
-          for (int m = i; m < j; m++) acc = fma(srow[m], Li[(size_t)m * nn + i], acc);
-          li = -acc * inv;
-        }
-        Li[(size_t)j * nn + i] = li;
-        LiT[(size_t)i * nn + j] = li;
+      // ---- FP64 phase B: row j of L^{-1} (and column j of its transpose):
+      // L^{-1}[j][i] = -inv sum_{i <= m < j} u_s[m] L^{-1}[m][i], a row of the transpose
+      double *lrow = ks;  // k_j(s) is no longer needed
+      split_rows(LiT, srow, nullptr, nullptr, nn, j, [](int i) { return i; },
+                 [j](int) { return j; }, part, [&](int i, double v, double) {
+                   const double li = -v * inv;
+                   lrow[i] = li;
+                   Li[(size_t)j * nn + i] = li;
+                   LiT[(size_t)i * nn + j] = li;
+                 });
+      if (tid == 0) {
+        lrow[j] = inv;
+        Li[(size_t)j * nn + j] = inv;
+        LiT[(size_t)j * nn + j] = inv;
       }
       __syncthreads();
-      // t1 = Kd Li[j]^T, t2 = Kdd Li[j]^T over rows a <= j (symmetric: entry (a,c) at row max)
-      for (int a = tid; a <= j; a += XB) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int c = 0; c <= j; c++) {
-          const int hi = a > c ? a : c, lo = a > c ? c : a;
-          const double lj = Li[(size_t)j * nn + c];
-          s1 = fma(Kd[(size_t)hi * nn + lo], lj, s1);
-          s2 = fma(Kdd[(size_t)hi * nn + lo], lj, s2);
-        }
-        t1[a] = s1;
-        t2[a] = s2;
-      }
-      __syncthreads();
+      // t1 = Kd Li[j]^T, t2 = Kdd Li[j]^T over rows a <= j
+      split_rows(Kd, lrow, Kdd, lrow, nn, j + 1, [](int) { return 0; }, [j](int) { return j + 1; },
+                 part, [&](int a, double v1, double v2) {
+                   t1[a] = v1;
+                   t2[a] = v2;
+                 });
       // row j of Q and R: (Li t)[b] = sum_{a <= b} Li[b][a] t[a]; Q is kept in full
-      for (int b = tid; b <= j; b += XB) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int a = 0; a <= b; a++) {
-          const double l = LiT[(size_t)a * nn + b];
-          s1 = fma(l, t1[a], s1);
-          s2 = fma(l, t2[a], s2);
-        }
-        Qf[(size_t)j * nn + b] = s1;
-        Qf[(size_t)b * nn + j] = s1;
-        qrow[b] = s1;
-        rrow[b] = s2;
-      }
-      __syncthreads();
+      split_rows(Li, t1, Li, t2, nn, j + 1, [](int) { return 0; }, [](int b) { return b + 1; },
+                 part, [&](int b, double v1, double v2) {
+                   Qf[(size_t)j * nn + b] = v1;
+                   Qf[(size_t)b * nn + j] = v1;
+                   qrow[b] = v1;
+                   rrow[b] = v2;
+                 });
       // r = Q ytil: old entries gain Q[j][i] ytil_j; entry j is row j of Q dotted with ytil
       const double ytj = sh_d[2];
       for (int i = tid; i < j; i += XB) {
@@ -713,10 +753,10 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
       if (tid == 0 && P.rescores) atomicAdd(P.rescores, 1);
       MRescore R;
       R.X = L.X; R.cnd = cnd; R.xl = xl; R.etab = etab; R.used = used; R.flg = flg; R.Jsc = Jsc;
-      R.dr = dr; R.LiT = LiT; R.Qf = Qf; R.ux = ux; R.yt = yt; R.r = r; R.wk = wk;
+      R.dg = dg; R.LiT = LiT; R.Qf = Qf; R.ux = ux; R.yt = yt; R.r = r; R.wk = wk;
       R.rlist = rlist; R.nlist = &sh_nlist; R.red_s = red_s; R.red_r = red_r;
       R.p = p; R.M = Q * 2 < M ? Q * 2 : M; R.jd = jn; R.nn = nn;
-      R.theta_inv = L.theta_inv; R.th2 = th2; R.onepg = L.onepg; R.psi = psi; R.vx = sh_vx;
+      R.theta_inv = L.theta_inv; R.ith2 = ith2; R.onepg = L.onepg; R.psi = psi; R.vx = sh_vx;
       R.F = F; R.dmux = dmux; R.wKdw = wKdw;
       const int b = mspe_rescore(R, R1 == 0x7fffffff ? INFINITY : B1);
       best = b;
@@ -724,7 +764,7 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
     __syncthreads();
     // the design (design indices), or -1 when a step failed; kernel (c) evaluates the
     // predictive equations on it in FP64
-    for (int i = tid; i < n; i += XB) L.idx[i] = sh_fail ? -1 : cnd[dr[i]];
+    for (int i = tid; i < n; i += XB) L.idx[i] = sh_fail ? -1 : dg[i];
   }
 }
 
@@ -735,7 +775,7 @@ size_t mxm_smem_bytes(int Mpad, int n) {
   const size_t nrow = (size_t)((n + 1) & ~1);
   return Qpad * 2 * sizeof(float4) + nrow * 2 * (sizeof(float4) + sizeof(float2)) +
          (size_t)n * 10 * sizeof(double) + (size_t)Mpad * sizeof(float) +
-         (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + 2 * (size_t)Mpad +
+         2 * (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + 2 * (size_t)Mpad +
          (size_t)RING * 2 * XB * sizeof(float4);
 }
 
