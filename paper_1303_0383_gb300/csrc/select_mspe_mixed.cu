@@ -274,11 +274,103 @@ struct MRescore {
   double theta_inv, ith2, onepg, psi, vx, F, dmux, wKdw;
 };
 
+// One candidate's J(c) in FP64 from scratch (one warp; RR rows of the design per lane):
+// u = L^{-1} k_c, ud = L^{-1} kd_c, Q u, then the sums of the FP64 kernel.  NaN when
+// v_j(c) <= 0.
+template <int RR>
+__device__ double rescore_one(const MRescore &R, int c, double dj) {
+  const int lane = threadIdx.x & 31;
+  const int jd = R.jd, nn = R.nn, p = R.p;
+  double *wkk = R.wk, *wkd = R.wk + nn, *wu = R.wk + 2 * nn, *wud = R.wk + 3 * nn;
+  const double *xc = R.X + (int64_t)R.cnd[c] * p;
+  for (int i = lane; i < jd; i += 32) {
+    const double *xi = R.X + (int64_t)R.dg[i] * p;
+    double acc = 0.0;
+    for (int k = 0; k < p; k++) {
+      const double t = xi[k] - xc[k];
+      acc = fma(t, t, acc);
+    }
+    const double kk = exp_nonpos(-acc * R.theta_inv, R.etab);
+    wkk[i] = kk;
+    wkd[i] = kk * acc * R.ith2;
+  }
+  __syncwarp();
+  // u = L^{-1} k_c and ud = L^{-1} kd_c: lane-owned rows i, L^{-1}[i][m] = LiT[m][i]
+  double au[RR], ad[RR];
+#pragma unroll
+  for (int rr = 0; rr < RR; rr++) au[rr] = ad[rr] = 0.0;
+  for (int m = 0; m < jd; m++) {
+    const double km = wkk[m], kdm = wkd[m];
+    const double *lt = R.LiT + (size_t)m * nn;
+#pragma unroll
+    for (int rr = 0; rr < RR; rr++) {
+      const int i = 32 * rr + lane;
+      if (i >= m && i < jd) {
+        const double l = lt[i];
+        au[rr] = fma(l, km, au[rr]);
+        ad[rr] = fma(l, kdm, ad[rr]);
+      }
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < RR; rr++) {
+    const int i = 32 * rr + lane;
+    if (i < jd) {
+      wu[i] = au[rr];
+      wud[i] = ad[rr];
+    }
+  }
+  __syncwarp();
+  // Q u (Q symmetric, stored in full)
+  double aq[RR];
+#pragma unroll
+  for (int rr = 0; rr < RR; rr++) aq[rr] = 0.0;
+  for (int a = 0; a < jd; a++) {
+    const double ua = wu[a];
+    const double *qa = R.Qf + (size_t)a * nn;
+#pragma unroll
+    for (int rr = 0; rr < RR; rr++) {
+      const int b = 32 * rr + lane;
+      if (b < jd) aq[rr] = fma(qa[b], ua, aq[rr]);
+    }
+  }
+  double s_uu = 0.0, s_ux = 0.0, s_kz = 0.0, s_pc = 0.0, s_mn = 0.0, s_qn = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < RR; rr++) {
+    const int i = 32 * rr + lane;
+    if (i < jd) {
+      const double u = au[rr], ud = ad[rr];
+      s_uu = fma(u, u, s_uu);
+      s_ux = fma(R.ux[i], u, s_ux);
+      s_kz = fma(ud, u, s_kz);
+      s_pc = fma(ud, R.yt[i], s_pc);
+      s_mn = fma(u, R.r[i], s_mn);
+      s_qn = fma(u, aq[rr], s_qn);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s_uu += __shfl_xor_sync(0xffffffffu, s_uu, o);
+    s_ux += __shfl_xor_sync(0xffffffffu, s_ux, o);
+    s_kz += __shfl_xor_sync(0xffffffffu, s_kz, o);
+    s_pc += __shfl_xor_sync(0xffffffffu, s_pc, o);
+    s_mn += __shfl_xor_sync(0xffffffffu, s_mn, o);
+    s_qn += __shfl_xor_sync(0xffffffffu, s_qn, o);
+  }
+  const double vc = R.onepg - s_uu;
+  if (!(vc > 0.0)) return NAN;
+  const double cx = corr64(R.xl, xc, p, R.theta_inv, R.etab) - s_ux;
+  const double Vc = R.psi * vc / dj;
+  const double dmuc = s_pc - s_mn;
+  const double dVc = (-R.wKdw * vc - R.psi * (2.0 * s_kz - s_qn)) / dj;
+  const double G = R.F + dVc * dVc / (2.0 * Vc * Vc) + dmuc * dmuc / Vc;
+  return R.psi / dj * (R.vx - cx * cx / vc) + R.dmux * R.dmux / G;
+}
+
 // Candidates within 2 DELTA of the screen's best (or flagged) are re-scored; returns (to
 // every thread, after a barrier) the rank of the FP64 minimum, or -1 when none is valid.
 __device__ int mspe_rescore(const MRescore &R, float B1) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int jd = R.jd, nn = R.nn, p = R.p;
+  const int jd = R.jd;
   if (tid == 0) *R.nlist = 0;
   __syncthreads();
   const float lim = B1 + 2.0f * DELTA * fabsf(B1);
@@ -292,99 +384,17 @@ __device__ int mspe_rescore(const MRescore &R, float B1) {
   __syncthreads();
   const bool all = *R.nlist > RESCORE_CAP;
   const int nl = all ? R.M : *R.nlist;
-  double *wkk = R.wk, *wkd = R.wk + nn, *wu = R.wk + 2 * nn, *wud = R.wk + 3 * nn;
   const double dj = (double)(jd - 2);
   double bs = INFINITY;
   int br = 0x7fffffff;
   for (int item = warp; item < nl; item += XB / 32) {
     const int c = all ? item : R.rlist[item];
     if (R.used[c]) continue;
-    const double *xc = R.X + (int64_t)R.cnd[c] * p;
-    for (int i = lane; i < jd; i += 32) {
-      const double *xi = R.X + (int64_t)R.dg[i] * p;
-      double acc = 0.0;
-      for (int k = 0; k < p; k++) {
-        const double t = xi[k] - xc[k];
-        acc = fma(t, t, acc);
-      }
-      const double kk = exp_nonpos(-acc * R.theta_inv, R.etab);
-      wkk[i] = kk;
-      wkd[i] = kk * acc * R.ith2;
-    }
-    __syncwarp();
-    // u = L^{-1} k_c and ud = L^{-1} kd_c: lane-owned rows i, L^{-1}[i][m] = LiT[m][i]
-    double au[kMaxN / 32], ad[kMaxN / 32];
-#pragma unroll
-    for (int rr = 0; rr < kMaxN / 32; rr++) au[rr] = ad[rr] = 0.0;
-    for (int m = 0; m < jd; m++) {
-      const double km = wkk[m], kdm = wkd[m];
-      const double *lt = R.LiT + (size_t)m * nn;
-#pragma unroll
-      for (int rr = 0; rr < kMaxN / 32; rr++) {
-        const int i = 32 * rr + lane;
-        if (i >= m && i < jd) {
-          const double l = lt[i];
-          au[rr] = fma(l, km, au[rr]);
-          ad[rr] = fma(l, kdm, ad[rr]);
-        }
-      }
-    }
-#pragma unroll
-    for (int rr = 0; rr < kMaxN / 32; rr++) {
-      const int i = 32 * rr + lane;
-      if (i < jd) {
-        wu[i] = au[rr];
-        wud[i] = ad[rr];
-      }
-    }
-    __syncwarp();
-    // Q u (Q symmetric, stored in full)
-    double aq[kMaxN / 32];
-#pragma unroll
-    for (int rr = 0; rr < kMaxN / 32; rr++) aq[rr] = 0.0;
-    for (int a = 0; a < jd; a++) {
-      const double ua = wu[a];
-      const double *qa = R.Qf + (size_t)a * nn;
-#pragma unroll
-      for (int rr = 0; rr < kMaxN / 32; rr++) {
-        const int b = 32 * rr + lane;
-        if (b < jd) aq[rr] = fma(qa[b], ua, aq[rr]);
-      }
-    }
-    double s_uu = 0.0, s_ux = 0.0, s_kz = 0.0, s_pc = 0.0, s_mn = 0.0, s_qn = 0.0;
-#pragma unroll
-    for (int rr = 0; rr < kMaxN / 32; rr++) {
-      const int i = 32 * rr + lane;
-      if (i < jd) {
-        const double u = au[rr], ud = ad[rr];
-        s_uu = fma(u, u, s_uu);
-        s_ux = fma(R.ux[i], u, s_ux);
-        s_kz = fma(ud, u, s_kz);
-        s_pc = fma(ud, R.yt[i], s_pc);
-        s_mn = fma(u, R.r[i], s_mn);
-        s_qn = fma(u, aq[rr], s_qn);
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s_uu += __shfl_xor_sync(0xffffffffu, s_uu, o);
-      s_ux += __shfl_xor_sync(0xffffffffu, s_ux, o);
-      s_kz += __shfl_xor_sync(0xffffffffu, s_kz, o);
-      s_pc += __shfl_xor_sync(0xffffffffu, s_pc, o);
-      s_mn += __shfl_xor_sync(0xffffffffu, s_mn, o);
-      s_qn += __shfl_xor_sync(0xffffffffu, s_qn, o);
-    }
-    const double vc = R.onepg - s_uu;
-    if (vc > 0.0) {
-      const double cx = corr64(R.xl, xc, p, R.theta_inv, R.etab) - s_ux;
-      const double Vc = R.psi * vc / dj;
-      const double dmuc = s_pc - s_mn;
-      const double dVc = (-R.wKdw * vc - R.psi * (2.0 * s_kz - s_qn)) / dj;
-      const double G = R.F + dVc * dVc / (2.0 * Vc * Vc) + dmuc * dmuc / Vc;
-      const double Jc = R.psi / dj * (R.vx - cx * cx / vc) + R.dmux * R.dmux / G;
-      if (Jc == Jc && j_better64(Jc, c, bs, br)) {
-        bs = Jc;
-        br = c;
-      }
+    // rows per lane sized to the design, so no FP64 instruction runs for absent rows
+    const double Jc = jd <= 64 ? rescore_one<2>(R, c, dj) : rescore_one<kMaxN / 32>(R, c, dj);
+    if (Jc == Jc && j_better64(Jc, c, bs, br)) {
+      bs = Jc;
+      br = c;
     }
     __syncwarp();  // the scratch is rewritten for the next candidate
   }
