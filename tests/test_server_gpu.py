@@ -25,18 +25,18 @@ def _designs():
     return ws, descs
 
 
-def _uniform(desc, w, XX, n, ncand, precision):
+def _uniform(desc, w, XX, n, ncand, precision, method="alc"):
     import torch
     out = lagp.predict_torch(desc["X"], desc["Z"], torch.as_tensor(XX, device="cuda"), w.n0, n,
-                             ncand, w.d, w.g, "alc", precision)
+                             ncand, w.d, w.g, method, precision)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_server_results_same_alone_and_in_the_mix(precision):
+@pytest.mark.parametrize("method,precision", [("alc", "mixed"), ("alc", "fp64"), ("mspe", "mixed")])
+def test_server_results_same_alone_and_in_the_mix(method, precision):
     ws, descs = _designs()
-    srv = lagp.Server(descs, "alc", precision, nmax=64, ncand_max=400, max_batch=2048,
+    srv = lagp.Server(descs, method, precision, nmax=64, ncand_max=400, max_batch=2048,
                       memory_budget=2 << 30, max_slots=3)
     try:
         rng = np.random.default_rng(7)
@@ -45,7 +45,7 @@ def test_server_results_same_alone_and_in_the_mix(precision):
         assert srv.wait(rid, 60000)
         alone = srv.results(rid)
         assert (alone["status"] == 0).all() and alone["latency_ms"] > 0
-        uni = _uniform(descs[1], ws[1], XR, 30, 200, precision)
+        uni = _uniform(descs[1], ws[1], XR, 30, 200, precision, method)
         assert np.array_equal(uni["idx"], alone["idx"])
         for k in ("mean", "s2", "var"):
             assert np.array_equal(uni[k], alone[k]), k
@@ -82,7 +82,7 @@ def test_server_results_same_alone_and_in_the_mix(precision):
         # spot-check some of the others against the uniform entry point
         for i, d, x, n, ncand in reqs[::6]:
             got = srv.results(i)
-            ref = _uniform(descs[d], ws[d], x, n, ncand, precision)
+            ref = _uniform(descs[d], ws[d], x, n, ncand, precision, method)
             assert np.array_equal(got["idx"], ref["idx"])
             assert np.array_equal(got["mean"], ref["mean"]) and np.array_equal(got["s2"], ref["s2"])
         st = srv.stats()
