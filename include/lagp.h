@@ -96,7 +96,9 @@ int lagp_design_destroy(lagp_design *d);
  * by `method`, predictive equations.  Host outputs (caller-owned): mean[T], s2[T];
  * var[T], idx[T x n] and status[T] may be NULL.  The call copies XX to the device,
  * runs kernels (a)-(c), copies the results back and synchronises.  Device memory for
- * inputs, outputs and scratch is allocated and freed inside the call. */
+ * inputs, outputs and scratch is taken from and returned to a memory pool of the
+ * library's own (one per device), which keeps up to 4 GiB of freed memory for the next
+ * call until the process exits. */
 int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, int32_t n,
                  int32_t ncand, double theta, double g, int32_t method, int32_t precision,
                  double *mean, double *s2, double *var, int32_t *idx, int8_t *status);

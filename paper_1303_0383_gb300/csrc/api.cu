@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 
 #include "internal.h"
@@ -215,6 +216,44 @@ int lagp_predict_dev(const double *X, const double *Z, int64_t N, int32_t p, con
                          s2, var, idx, status, rest, rest_bytes, stream);
 }
 
+namespace {
+
+// The host entry point's device blocks come from a pool of the library's own per device,
+// which keeps up to kPoolKeep bytes of freed memory mapped for the next call (the default
+// pool returns everything at each synchronisation, and re-mapping a few hundred MB of
+// workspace costs about a millisecond per call).
+constexpr uint64_t kPoolKeep = 4ull << 30;
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+int lib_pool(int device, cudaMemPool_t *out) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(device);
+  if (it != g_pools.end()) {
+    *out = it->second;
+    return LAGP_OK;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaMemPool_t pool;
+  cudaError_t e = cudaMemPoolCreate(&pool, &props);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint64_t keep = kPoolKeep;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (e != cudaSuccess) {
+    cudaMemPoolDestroy(pool);
+    return cuda_status(e);
+  }
+  g_pools[device] = pool;
+  *out = pool;
+  return LAGP_OK;
+}
+
+}  // namespace
+
 int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, int32_t n,
                  int32_t ncand, double theta, double g, int32_t method, int32_t precision,
                  double *mean, double *s2, double *var, int32_t *idx, int8_t *status) {
@@ -245,7 +284,10 @@ int lagp_predict(const lagp_design *d, const double *XX, int64_t T, int32_t n0, 
   size_t off_ws = align_up(off_st + nT, 256);
   size_t total = off_ws + ws_bytes;
   char *buf = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void **>(&buf), total, s);
+  cudaMemPool_t pool;
+  st = lib_pool(d->device, &pool);
+  if (st) return st;
+  e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&buf), total, pool, s);
   if (e != cudaSuccess) return cuda_status(e);
   double *dXX = reinterpret_cast<double *>(buf + off_xx);
   double *dmean = reinterpret_cast<double *>(buf + off_mean);
