@@ -132,10 +132,6 @@ __device__ __forceinline__ double corr64(const double *a, const double *b, int p
 // row is consumed.  Each thread waits only for its own copies (no barrier).
 constexpr int RING_A = 4;  // stages per thread, where the ring is used
 
-__device__ __forceinline__ void cp_async16(float4 *smem_dst, const float4 *gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -147,6 +143,23 @@ __device__ __forceinline__ unsigned long long l2_evict_last_policy() {
   unsigned long long pol;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
+}
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ double ld_l2_hint(const double *a, unsigned long long pol) {
+  double v;
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void cp_async16_l2_hint(float4 *smem_dst, const float4 *gmem_src,
+                                                   unsigned long long pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s),
+               "l"(gmem_src), "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ float4 ld_l2_hint(const float4 *a, unsigned long long pol) {
   float4 v;
@@ -184,10 +197,14 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsig
                                             float &b1, int &r1, float &b2) {
   const int nt = blockDim.x;
   const int jr = C.j < C.R ? C.j : C.R;  // rows R .. j-1 come from global memory
-  // the first RA - 1 global rows start on their way (one copy group each)
+  // the first RA - 1 global rows start on their way (one copy group each); streamed rows
+  // do not fit in L2 anyway, so they go evict-first and leave it to the data re-read every
+  // step (candidate coordinates; 8-d workload 156.2 -> 140.5 ms)
+  const unsigned long long polf = l2_evict_first_policy();
 #pragma unroll
   for (int st = 0; st < RA - 1; st++) {
-    if (jr + st < C.j) cp_async16(C.ring + st * nt, C.U + (size_t)(jr + st) * C.Qpad + q);
+    if (jr + st < C.j)
+      cp_async16_l2_hint(C.ring + st * nt, C.U + (size_t)(jr + st) * C.Qpad + q, polf);
     cp_async_commit();
   }
   // squared distance of the pair to the new point
@@ -221,7 +238,7 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsig
     int sc = 0, sp = RA - 1;  // ring stages of rows i and i + RA - 1
     for (int i = jr; i < C.j; i++) {
       const int ip = i + RA - 1;
-      if (ip < C.j) cp_async16(C.ring + sp * nt, C.U + (size_t)ip * C.Qpad + q);
+      if (ip < C.j) cp_async16_l2_hint(C.ring + sp * nt, C.U + (size_t)ip * C.Qpad + q, polf);
       cp_async_commit();
       cp_async_wait<RA - 1>();  // row i has landed
       const float4 b = C.ring[sc * nt];

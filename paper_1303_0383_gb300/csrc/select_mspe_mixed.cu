@@ -38,7 +38,7 @@ constexpr int XB = 256;  // threads per CTA
 // through a ring of RING stages in shared memory with asynchronous copies (cp.async), so
 // that RING - 1 rows of both arrays are on their way while one is consumed.  The arrays
 // exceed L2 on the large workloads and the loop is bound by the bytes in flight per SM.
-// (cp_async16 and its groups: mixed_screen.cuh)
+// (the asynchronous copies and their groups: mixed_screen.cuh)
 constexpr int RING = 6;
 
 struct MxParams {
@@ -75,7 +75,9 @@ __device__ __forceinline__ bool j_better64(double a, int ra, double b, int rb) {
 // all warps of the CTA issue FP64 work and each chain is SPLIT times shorter; the partial
 // sums meet in `part` (shared memory) and are added in a fixed order, so the result does
 // not depend on the schedule.  Ends with the outputs written through out(i, y1, y2) and a
-// barrier.
+// barrier.  The matrices are read at every step of the location and are kept in L2 ahead
+// of the candidates' factor rows, which stream through with an evict-first policy
+// (8-d workload 393 -> 374 ms, paper-2d 76.5 -> 70.1 ms).
 constexpr int SPLIT = 4;
 template <class Lo, class Hi, class Out>
 __device__ __forceinline__ void split_rows(const double *A1, const double *x1, const double *A2,
@@ -88,9 +90,10 @@ __device__ __forceinline__ void split_rows(const double *A1, const double *x1, c
       const double *a1 = A1 + (size_t)i * nn, *a2 = A2 ? A2 + (size_t)i * nn : nullptr;
       double s1 = 0.0, s2 = 0.0;
       const int h = hi(i);
+      const unsigned long long pol = l2_evict_last_policy();
       for (int m = lo(i) + c; m < h; m += SPLIT) {
-        s1 = fma(a1[m], x1[m], s1);
-        if (a2) s2 = fma(a2[m], x2[m], s2);
+        s1 = fma(ld_l2_hint(a1 + m, pol), x1[m], s1);
+        if (a2) s2 = fma(ld_l2_hint(a2 + m, pol), x2[m], s2);
       }
       part[2 * tid] = s1;
       part[2 * tid + 1] = s2;
@@ -151,11 +154,12 @@ struct MStep {
 __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned char *used,
                                           float &b1, int &r1, float &b2, int &nf) {
   // the first RING - 1 rows start on their way (one copy group per row, empty past row j)
+  const unsigned long long pol = l2_evict_first_policy();
 #pragma unroll
   for (int st = 0; st < RING - 1; st++) {
     if (st < C.j) {
-      cp_async16(C.ring + (2 * st) * XB, C.U + (size_t)st * C.Qpad + q);
-      cp_async16(C.ring + (2 * st + 1) * XB, C.Ud + (size_t)st * C.Qpad + q);
+      cp_async16_l2_hint(C.ring + (2 * st) * XB, C.U + (size_t)st * C.Qpad + q, pol);
+      cp_async16_l2_hint(C.ring + (2 * st + 1) * XB, C.Ud + (size_t)st * C.Qpad + q, pol);
     }
     cp_async_commit();
   }
@@ -182,8 +186,8 @@ __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned 
   for (int i = 0; i < C.j; i++) {
     const int ip = i + RING - 1;
     if (ip < C.j) {  // refill the stage consumed at row i - 1
-      cp_async16(C.ring + (2 * sp) * XB, C.U + (size_t)ip * C.Qpad + q);
-      cp_async16(C.ring + (2 * sp + 1) * XB, C.Ud + (size_t)ip * C.Qpad + q);
+      cp_async16_l2_hint(C.ring + (2 * sp) * XB, C.U + (size_t)ip * C.Qpad + q, pol);
+      cp_async16_l2_hint(C.ring + (2 * sp + 1) * XB, C.Ud + (size_t)ip * C.Qpad + q, pol);
     }
     cp_async_commit();
     cp_async_wait<RING - 1>();  // row i has landed
