@@ -39,6 +39,8 @@ constexpr int XB = 256;  // threads per CTA
 // that RING - 1 rows of both arrays are on their way while one is consumed.  The arrays
 // exceed L2 on the large workloads and the loop is bound by the bytes in flight per SM.
 // (the asynchronous copies and their groups: mixed_screen.cuh)
+// Where the ring does not fit in shared memory (the largest candidate counts) the kernel
+// is instantiated without it (RG = 0) and loads the rows straight into registers.
 constexpr int RING = 6;
 
 struct MxParams {
@@ -151,12 +153,13 @@ struct MStep {
 };
 
 // One step for one pair of candidates (2q, 2q+1).
+template <int RG>
 __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned char *used,
                                           float &b1, int &r1, float &b2, int &nf) {
   // the first RING - 1 rows start on their way (one copy group per row, empty past row j)
   const unsigned long long pol = l2_evict_first_policy();
 #pragma unroll
-  for (int st = 0; st < RING - 1; st++) {
+  for (int st = 0; st < RG - 1; st++) {
     if (st < C.j) {
       cp_async16_l2_hint(C.ring + (2 * st) * XB, C.U + (size_t)st * C.Qpad + q, pol);
       cp_async16_l2_hint(C.ring + (2 * st + 1) * XB, C.Ud + (size_t)st * C.Qpad + q, pol);
@@ -182,18 +185,26 @@ __device__ __forceinline__ void mspe_pair(const MStep &C, int q, const unsigned 
   const ff2 kdc = ff2_mul(ff2_mul(kc, arg), C.thinv);                     // Kd(s, c)
   // K(s,c) - u_s.u_c, Kd(s,c) - u_s.ud_c and q_j.u_c (compensated, Dot2)
   ff2acc a1{kc.h, kc.l}, a2{kdc.h, kdc.l}, a3{f2s(0.0f), f2s(0.0f)};
-  int sc = 0, sp = RING - 1;  // ring stages of rows i and i + RING - 1
+  int sc = 0, sp = RG - 1;  // ring stages of rows i and i + RG - 1
+#pragma unroll (RG ? 1 : 2)
   for (int i = 0; i < C.j; i++) {
-    const int ip = i + RING - 1;
-    if (ip < C.j) {  // refill the stage consumed at row i - 1
-      cp_async16_l2_hint(C.ring + (2 * sp) * XB, C.U + (size_t)ip * C.Qpad + q, pol);
-      cp_async16_l2_hint(C.ring + (2 * sp + 1) * XB, C.Ud + (size_t)ip * C.Qpad + q, pol);
+    float4 bu, bd;
+    if constexpr (RG > 0) {
+      const int ip = i + RG - 1;
+      if (ip < C.j) {  // refill the stage consumed at row i - 1
+        cp_async16_l2_hint(C.ring + (2 * sp) * XB, C.U + (size_t)ip * C.Qpad + q, pol);
+        cp_async16_l2_hint(C.ring + (2 * sp + 1) * XB, C.Ud + (size_t)ip * C.Qpad + q, pol);
+      }
+      cp_async_commit();
+      cp_async_wait<RG - 1>();  // row i has landed
+      bu = C.ring[(2 * sc) * XB];
+      bd = C.ring[(2 * sc + 1) * XB];
+      sc = (sc == RG - 1) ? 0 : sc + 1;
+      sp = (sp == RG - 1) ? 0 : sp + 1;
+    } else {
+      bu = ld_l2_hint(C.U + (size_t)i * C.Qpad + q, pol);
+      bd = ld_l2_hint(C.Ud + (size_t)i * C.Qpad + q, pol);
     }
-    cp_async_commit();
-    cp_async_wait<RING - 1>();  // row i has landed
-    const float4 bu = C.ring[(2 * sc) * XB], bd = C.ring[(2 * sc + 1) * XB];
-    sc = (sc == RING - 1) ? 0 : sc + 1;
-    sp = (sp == RING - 1) ? 0 : sp + 1;
     const float4 sa = C.sr4[i], qa = C.qr4[i];
     const float2 sl = C.sr2[i], ql = C.qr2[i];
     ff2acc_sub_prod(a1, sa, sl, bu);
@@ -420,6 +431,7 @@ __device__ int mspe_rescore(const MRescore &R, float B1) {
   return b == 0x7fffffff ? -1 : b;
 }
 
+template <int RG>
 __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kernel(MxParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, Mpad = P.Mpad, nn = P.nmax;
@@ -446,7 +458,7 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
   int *rlist = dg + ((nn + 3) & ~3);                // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   unsigned char *flg = used + Mpad;                                             // Mpad
-  float4 *ring = reinterpret_cast<float4 *>(flg + Mpad) + threadIdx.x;  // RING x 2 x XB
+  float4 *ring = reinterpret_cast<float4 *>(flg + Mpad) + threadIdx.x;  // RG x 2 x XB
   // the FP64 step's partial sums (2 x XB doubles) reuse the ring, idle outside the screen
   double *part = reinterpret_cast<double *>(flg + Mpad);
   __shared__ float tabh[64], tabl[64];
@@ -740,7 +752,7 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
       int r1 = 0x7fffffff, nf = 0;
       for (int q = tid; q < Q; q += XB) {
         if (used[2 * q] && used[2 * q + 1]) continue;
-        mspe_pair(C, q, used, b1, r1, b2, nf);
+        mspe_pair<RG>(C, q, used, b1, r1, b2, nf);
       }
       // best and second-best screen scores (double-buffered by step parity)
       const int par = j & 1;
@@ -784,13 +796,16 @@ __global__ void __launch_bounds__(XB, LAGP_MSPE_MIX_MINB) select_mspe_mixed_kern
 
 int mxm_mpad(int M) { return (int)align_up((size_t)M, 64); }
 
-size_t mxm_smem_bytes(int Mpad, int n) {
+// Dynamic shared memory with a ring of RG stages (RG = 0: no ring, only the FP64 step's
+// partial sums, which otherwise live in the ring).
+size_t mxm_smem_bytes(int Mpad, int n, int RG) {
   const size_t Qpad = (size_t)Mpad / 2;
   const size_t nrow = (size_t)((n + 1) & ~1);
+  const size_t tail = RG ? (size_t)RG * 2 * XB * sizeof(float4) : (size_t)2 * XB * sizeof(double);
   return Qpad * 2 * sizeof(float4) + nrow * 2 * (sizeof(float4) + sizeof(float2)) +
          (size_t)n * 10 * sizeof(double) + (size_t)Mpad * sizeof(float) +
          2 * (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + 2 * (size_t)Mpad +
-         (size_t)RING * 2 * XB * sizeof(float4);
+         tail;
 }
 
 int mxm_grid(int64_t T, int num_sms) {
@@ -836,14 +851,20 @@ int mxm_run(MxParams P, const MxLayout &L, int G, char *w, int32_t *user_idx, co
   P.Wk = reinterpret_cast<double *>(w + off); off += L.wk;
   P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(w + off);
   off += L.idx;
-  const size_t smem = mxm_smem_bytes(P.Mpad, P.nmax);
+  const bool ring = mxm_smem_bytes(P.Mpad, P.nmax, RING) <= di.smem_optin;
+  const size_t smem = mxm_smem_bytes(P.Mpad, P.nmax, ring ? RING : 0);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = cudaFuncSetAttribute(select_mspe_mixed_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ring ? cudaFuncSetAttribute(select_mspe_mixed_kernel<RING>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(select_mspe_mixed_kernel<0>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaMemsetAsync(w, 0, 512, stream);  // work counter and re-score counter
   if (e != cudaSuccess) return cuda_status(e);
-  select_mspe_mixed_kernel<<<G, XB, smem, stream>>>(P);
+  if (ring)
+    select_mspe_mixed_kernel<RING><<<G, XB, smem, stream>>>(P);
+  else
+    select_mspe_mixed_kernel<0><<<G, XB, smem, stream>>>(P);
   g_launches.fetch_add(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);

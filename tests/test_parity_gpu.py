@@ -297,3 +297,29 @@ def test_smooth_8d_full_size_sampled(method, precision):
     locs = np.random.default_rng(9).choice(w.T, size=10, replace=False)
     g, infos, bad = run_parity(w, locs=locs, method=method, precision=precision)
     assert not bad, bad[:3]
+
+
+# ----------------------------------------------------------------- largest sizes
+
+@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
+                                              ("mspe", "mixed")])
+def test_largest_candidate_count_parity(method, precision):
+    # 8192 candidates, the largest accepted: the mixed MSPE kernel runs without its row ring
+    # here (its shared memory would not fit)
+    w = inputs.random_case(31, 9000, 2, 2, 6, 40, 8192, d=0.2)
+    g, infos, bad = run_parity(w, method=method, precision=precision)
+    assert not bad, bad[:3]
+
+
+@pytest.mark.parametrize("method", ["alc", "mspe"])
+def test_largest_design_and_candidate_count_run(method):
+    # n = 256 and 8192 candidates (both limits): both precisions run, and the mixed designs
+    # and values agree with the FP64 ones (the oracle would take minutes here)
+    w = inputs.random_case(32, 9000, 2, 2, 6, 256, 8192, d=0.2, g=1e-4)
+    f = gpu_predict(w, method, "fp64")
+    m = gpu_predict(w, method, "mixed")
+    assert (f["status"] == 0).all() and (m["status"] == 0).all()
+    assert np.array_equal(f["idx"][:, :w.n0], m["idx"][:, :w.n0])
+    same = (f["idx"] == m["idx"]).all(axis=1)
+    rel = np.abs(f["s2"][same] - m["s2"][same]) / f["s2"][same]
+    assert same.any() and rel.max() <= 1e-9, (same, rel)
