@@ -18,8 +18,8 @@
 // where l' points outward.
 //
 // One CTA per location.  Per iteration, in FP64: K and Kd (one exp per pair), the
-// Cholesky factor (fp64_chol.cuh), L^-1 by forward substitution row by row,
-// K^-1 = L^-T L^-1 and the O(n^2) vector terms; the n^3 product K^-1 Kd behind
+// Cholesky factor (fp64_chol.cuh), L^-1 by forward substitution (right-looking, one barrier
+// per column), K^-1 = L^-T L^-1 and the O(n^2) vector terms; the n^3 product K^-1 Kd behind
 // tr((K^-1 Kd)^2) runs in float-float on the FP32 pipes (K^-1 has large entries of both
 // signs, so plain FP32 would leave l'' without a correct digit; float-float keeps about
 // 48 bits per product).  The matrices live in shared memory
@@ -56,11 +56,11 @@ struct MleParams {
   int *queue;
 };
 
-// Per-CTA buffers: four n x n FP64 matrices (squared distances, L then L^-1, Kd, K^-1)
-// and five FP64 vectors.
+// Per-CTA buffers: four n x n FP64 matrices (squared distances, L then K^-1, Kd, L^-1)
+// and four FP64 vectors.
 size_t mle_set_bytes(int n) {
   const size_t nn = (size_t)n * n;
-  return nn * 4 * sizeof(double) + (size_t)n * 5 * sizeof(double);
+  return nn * 4 * sizeof(double) + (size_t)n * 4 * sizeof(double);
 }
 
 __device__ double block_sum(double v, double *red) {
@@ -80,10 +80,10 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
   unsigned char *base = P.in_smem ? smraw : P.slots + (size_t)blockIdx.x * P.slot_bytes;
   const size_t nn = (size_t)nmax * nmax;
   double *R2 = reinterpret_cast<double *>(base);
-  double *Lm = R2 + nn;      // K, then its Cholesky factor L, then L^-1 (lower triangles)
+  double *Lm = R2 + nn;      // K, then its Cholesky factor L (lower triangles), then K^-1
   double *Kd = Lm + nn;
   double *Ki = Kd + nn;
-  double *Y = Ki + nn, *w = Y + nmax, *kdw = w + nmax, *tmp = kdw + nmax, *rl = tmp + nmax;
+  double *Y = Ki + nn, *w = Y + nmax, *kdw = w + nmax, *rl = kdw + nmax;
   __shared__ double etab[64];
   __shared__ double red[LB / 32];
   __shared__ double sh_th, sh_lo, sh_hi;
@@ -124,49 +124,62 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
         R2[e] = r2;
       }
     }
+    __syncthreads();  // R2 is read by other threads below
     while (!sh_fail && !sh_done) {
       const double th = sh_th;
       const double tinv = 1.0 / th, tinv2 = tinv * tinv;
-      // K (lower triangle) and Kd (full)
-      for (int e = tid; e < n * n; e += LB) {
-        const int a = e / n, b = e % n;
+      // K (lower triangle) and Kd (full): one exp per pair a > b, mirrored
+      const int ntri = n * (n + 1) / 2;
+      for (int e = tid; e < ntri; e += LB) {
+        const int a = tri_row(e), b = e - a * (a + 1) / 2;
         if (a == b) {
-          Lm[e] = 1.0 + P.g;
-          Kd[e] = 0.0;
+          Lm[a * lda + a] = 1.0 + P.g;
+          Kd[a * lda + a] = 0.0;
         } else {
-          const double r2 = R2[e];
+          const double r2 = R2[a * lda + b];
           const double k = exp_nonpos(-r2 * tinv, etab);
-          if (b < a) Lm[e] = k;
-          Kd[e] = k * r2 * tinv2;
+          Lm[a * lda + b] = k;
+          const double kd = k * r2 * tinv2;
+          Kd[a * lda + b] = kd;
+          Kd[b * lda + a] = kd;
         }
       }
       chol_flat_fp64(Lm, n, lda, 0, rl, &sh_fail);
       if (sh_fail) break;
-      // L^-1 in place, row by row: x_ic = -(sum_{c<=m<i} l_im x_mc) / l_ii, x_ii = 1 / l_ii
-      for (int i = 0; i < n; i++) {
-        for (int c = tid; c <= i; c += LB) {
-          double s = 0.0;
-          for (int m = c; m < i; m++) s = fma(Lm[i * lda + m], Lm[m * lda + c], s);
-          tmp[c] = (c == i) ? rl[i] : -s * rl[i];
+      // X = L^-1 (lower triangle, in Ki's storage): x_ic = -(sum_{c<=m<i} l_im x_mc) / l_ii,
+      // x_ii = 1 / l_ii.  Right-looking: at step m every entry (i > m, c <= m) takes its
+      // term l_im x_mc -- the same terms in the same order as the row-by-row sums -- and
+      // the thread that adds the last term of row m + 1 finishes that entry, so a step is
+      // one barrier and all threads share its FP64 work.
+      double *Xb = Ki;
+      for (int e = tid; e < ntri; e += LB) {
+        const int a = tri_row(e), b = e - a * (a + 1) / 2;
+        Xb[a * lda + b] = (a == b) ? rl[a] : 0.0;
+      }
+      __syncthreads();
+      for (int m = 0; m < n - 1; m++) {
+        const int w1 = m + 1, cnt = (n - 1 - m) * w1;
+        for (int e = tid; e < cnt; e += LB) {
+          const int i = m + 1 + e / w1, c = e % w1;
+          const double sv = fma(Lm[i * lda + m], Xb[m * lda + c], Xb[i * lda + c]);
+          Xb[i * lda + c] = (i == m + 1) ? -sv * rl[i] : sv;
         }
         __syncthreads();
-        for (int c = tid; c <= i; c += LB) Lm[i * lda + c] = tmp[c];
-        __syncthreads();
       }
-      // K^-1 = L^-T L^-1 (both triangles)
-      for (int e = tid; e < n * n; e += LB) {
-        const int a = e / n, b = e % n;
-        if (b > a) continue;
+      // K^-1 = X^T X (both triangles) into L's storage, which is no longer needed
+      double *KiM = Lm;
+      for (int e = tid; e < ntri; e += LB) {
+        const int a = tri_row(e), b = e - a * (a + 1) / 2;
         double s = 0.0;
-        for (int m = a; m < n; m++) s = fma(Lm[m * lda + a], Lm[m * lda + b], s);
-        Ki[a * lda + b] = s;
-        Ki[b * lda + a] = s;
+        for (int m = a; m < n; m++) s = fma(Xb[m * lda + a], Xb[m * lda + b], s);
+        KiM[a * lda + b] = s;
+        KiM[b * lda + a] = s;
       }
       __syncthreads();
       // w = K^-1 Y, then Kd w
       for (int a = tid; a < n; a += LB) {
         double s = 0.0;
-        for (int b = 0; b < n; b++) s = fma(Ki[a * lda + b], Y[b], s);
+        for (int b = 0; b < n; b++) s = fma(KiM[a * lda + b], Y[b], s);
         w[a] = s;
       }
       __syncthreads();
@@ -184,7 +197,7 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
         double sdd = 0.0, sq2 = 0.0, st1 = 0.0, st3 = 0.0;
         for (int b = 0; b < n; b++) {
           const double kd = Kd[a * lda + b], kdd = kd * (R2[a * lda + b] * tinv2 - 2.0 * tinv);
-          const double ki = Ki[a * lda + b];
+          const double ki = KiM[a * lda + b];
           sdd = fma(kdd, w[b], sdd);
           sq2 = fma(ki, kdw[b], sq2);
           st1 = fma(ki, kd, st1);
@@ -199,11 +212,11 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
       // tr((K^-1 Kd)^2) = sum_ab A_ab A_ba with A = K^-1 Kd, the n^3 term: formed in
       // float-float on the FP32 pipes (compensated dots, about 2^-48 per product).  It
       // enters l'' only, which sets the Newton step, not the root l' = 0 the iteration
-      // converges to.  K^-1 goes to L^-1's storage (no longer needed) and Kd is converted
-      // in place (its FP64 uses are done), one float-float pair per FP64 slot.
-      float2 *Kif = reinterpret_cast<float2 *>(Lm), *Kdf = reinterpret_cast<float2 *>(Kd);
+      // converges to.  K^-1 and Kd are converted in place (their FP64 uses are done), one
+      // float-float pair per FP64 slot.
+      float2 *Kif = reinterpret_cast<float2 *>(KiM), *Kdf = reinterpret_cast<float2 *>(Kd);
       for (int e = tid; e < n * n; e += LB) {
-        const ff ki = ff_from_double(Ki[e]), kd = ff_from_double(Kd[e]);
+        const ff ki = ff_from_double(KiM[e]), kd = ff_from_double(Kd[e]);
         Kif[e] = make_float2(ki.h, ki.l);
         Kdf[e] = make_float2(kd.h, kd.l);
       }
