@@ -56,11 +56,14 @@ struct MleParams {
   int *queue;
 };
 
-// Per-CTA buffers: four n x n FP64 matrices (squared distances, L then K^-1, Kd, L^-1)
-// and four FP64 vectors.
+// Per-CTA buffers: three n x n FP64 matrices (L then K^-1, Kd, L^-1), four FP64 vectors
+// and the design's coordinates (up to kMaxP per point).  Squared distances are recomputed
+// from the coordinates where needed (p operations each, in the same order every time),
+// which leaves room for three CTAs per SM at n = 50: the Cholesky's pivot chain is
+// sequential, and more locations in flight hide it.
 size_t mle_set_bytes(int n) {
   const size_t nn = (size_t)n * n;
-  return nn * 4 * sizeof(double) + (size_t)n * 4 * sizeof(double);
+  return nn * 3 * sizeof(double) + (size_t)n * (4 + kMaxP) * sizeof(double);
 }
 
 __device__ double block_sum(double v, double *red) {
@@ -79,11 +82,11 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
   const int nmax = P.n;
   unsigned char *base = P.in_smem ? smraw : P.slots + (size_t)blockIdx.x * P.slot_bytes;
   const size_t nn = (size_t)nmax * nmax;
-  double *R2 = reinterpret_cast<double *>(base);
-  double *Lm = R2 + nn;      // K, then its Cholesky factor L (lower triangles), then K^-1
+  double *Lm = reinterpret_cast<double *>(base);  // K, its Cholesky factor L, then K^-1
   double *Kd = Lm + nn;
   double *Ki = Kd + nn;
   double *Y = Ki + nn, *w = Y + nmax, *kdw = w + nmax, *rl = kdw + nmax;
+  double *xd = rl + nmax;    // nmax x p coordinates of the design
   __shared__ double etab[64];
   __shared__ double red[LB / 32];
   __shared__ double sh_th, sh_lo, sh_hi;
@@ -113,18 +116,18 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
     __syncthreads();
     if (!sh_fail) {
       for (int i = tid; i < n; i += LB) Y[i] = P.Z[d[i]];
-      for (int e = tid; e < n * n; e += LB) {
-        const int a = e / n, b = e % n;
-        const double *xa = P.X + (int64_t)d[a] * p, *xb = P.X + (int64_t)d[b] * p;
-        double r2 = 0.0;
-        for (int k = 0; k < p; k++) {
-          const double t = xa[k] - xb[k];
-          r2 = fma(t, t, r2);
-        }
-        R2[e] = r2;
-      }
+      for (int e = tid; e < n * p; e += LB) xd[e] = P.X[(int64_t)d[e / p] * p + e % p];
     }
-    __syncthreads();  // R2 is read by other threads below
+    __syncthreads();  // the coordinates are read by other threads below
+    // squared distance of design points a and b
+    auto r2of = [&](int a, int b) {
+      double r2 = 0.0;
+      for (int k = 0; k < p; k++) {
+        const double t = xd[a * p + k] - xd[b * p + k];
+        r2 = fma(t, t, r2);
+      }
+      return r2;
+    };
     while (!sh_fail && !sh_done) {
       const double th = sh_th;
       const double tinv = 1.0 / th, tinv2 = tinv * tinv;
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
           Lm[a * lda + a] = 1.0 + P.g;
           Kd[a * lda + a] = 0.0;
         } else {
-          const double r2 = R2[a * lda + b];
+          const double r2 = r2of(a, b);
           const double k = exp_nonpos(-r2 * tinv, etab);
           Lm[a * lda + b] = k;
           const double kd = k * r2 * tinv2;
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
         q3 = fma(w[a], kdw[a], q3);
         double sdd = 0.0, sq2 = 0.0, st1 = 0.0, st3 = 0.0;
         for (int b = 0; b < n; b++) {
-          const double kd = Kd[a * lda + b], kdd = kd * (R2[a * lda + b] * tinv2 - 2.0 * tinv);
+          const double kd = Kd[a * lda + b], kdd = kd * (r2of(a, b) * tinv2 - 2.0 * tinv);
           const double ki = KiM[a * lda + b];
           sdd = fma(kdd, w[b], sdd);
           sq2 = fma(ki, kdw[b], sq2);
