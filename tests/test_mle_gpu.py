@@ -73,7 +73,8 @@ def test_mle_boundary_and_per_location_start():
     assert (np.abs(th2 - ref["theta"]) / ref["theta"]).max() <= 1e-7
 
 
-def test_select_with_per_location_theta_matches_oracle():
+@pytest.mark.parametrize("method", ["alc", "mspe"])
+def test_select_with_per_location_theta_matches_oracle(method):
     torch = _torch()
     w = inputs.tiny_2d()
     T = w.T
@@ -83,10 +84,10 @@ def test_select_with_per_location_theta_matches_oracle():
     idx = torch.empty((T, w.n), dtype=torch.int32, device="cuda")
     st = torch.empty(T, dtype=torch.int8, device="cuda")
     for precision in ("fp64", "mixed"):
-        ws = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, w.n, w.ncand, "alc", precision))
+        ws = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, w.n, w.ncand, method, precision))
         lagp.lagp_select_theta_dev(dev(w.X, torch.float64), dev(w.Z, torch.float64),
                                    dev(w.XX, torch.float64), dev(cand, torch.int32), w.n0, w.n,
-                                   dev(thetas, torch.float64), w.g, "alc", precision, out["mean"],
+                                   dev(thetas, torch.float64), w.g, method, precision, out["mean"],
                                    out["s2"], out["var"], idx, st, ws)
         torch.cuda.synchronize()
         assert int(st.abs().sum()) == 0
@@ -94,7 +95,7 @@ def test_select_with_per_location_theta_matches_oracle():
         gi = idx.cpu().numpy()
         for t in range(0, T, 5):
             wt = dataclasses.replace(w, d=float(thetas[t]))
-            info = check_location(wt, t, cand[t], gi[t], g["mean"][t], g["s2"][t], "alc",
+            info = check_location(wt, t, cand[t], gi[t], g["mean"][t], g["s2"][t], method,
                                   gpu_var=g["var"][t])
             assert info["ok_vals"], (precision, info)
 
@@ -129,14 +130,14 @@ def test_design_predict_matches_oracle():
         assert ok, t
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_two_stage_scheme_stage_by_stage(precision):
+@pytest.mark.parametrize("method,precision", [("alc", "fp64"), ("alc", "mixed"), ("mspe", "mixed")])
+def test_two_stage_scheme_stage_by_stage(method, precision):
     torch = _torch()
     w = inputs.tiny_2d()
     T, n = w.T, w.n
     tmin, tmax = w.d / 100, w.d * 100
     Xd, Zd, XXd = dev(w.X, torch.float64), dev(w.Z, torch.float64), dev(w.XX, torch.float64)
-    r = lagp.predict_stagewise(Xd, Zd, XXd, w.n0, n, w.ncand, w.d, w.g, "alc", precision, stages=2)
+    r = lagp.predict_stagewise(Xd, Zd, XXd, w.n0, n, w.ncand, w.d, w.g, method, precision, stages=2)
     torch.cuda.synchronize()
     g = {k: v.cpu().numpy() for k, v in r.items()}
     assert (g["status"] == 0).all() and (g["mle_status"] == 0).all()
@@ -147,22 +148,22 @@ def test_two_stage_scheme_stage_by_stage(precision):
     s2, var = torch.empty_like(mean), torch.empty_like(mean)
     idx = torch.empty((T, n), dtype=torch.int32, device="cuda")
     st = torch.empty(T, dtype=torch.int8, device="cuda")
-    ws = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, n, w.ncand, "alc", precision))
-    lagp.lagp_select_dev(Xd, Zd, XXd, cd, w.n0, n, w.d, w.g, "alc", precision, mean, s2, var, idx,
+    ws = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, n, w.ncand, method, precision))
+    lagp.lagp_select_dev(Xd, Zd, XXd, cd, w.n0, n, w.d, w.g, method, precision, mean, s2, var, idx,
                          st, ws)
     idx1 = idx.cpu().numpy()
     th1, _, st1 = gpu_mle(w, idx1, w.d, tmin, tmax)
     assert (st1 == 0).all()
     ref1 = oracle.mle_batch(w.X, w.Z, idx1, w.d, w.g, tmin, tmax)
     assert (np.abs(th1 - ref1["theta"]) / ref1["theta"]).max() <= THETA_RTOL
-    lagp.lagp_select_theta_dev(Xd, Zd, XXd, cd, w.n0, n, dev(th1, torch.float64), w.g, "alc",
+    lagp.lagp_select_theta_dev(Xd, Zd, XXd, cd, w.n0, n, dev(th1, torch.float64), w.g, method,
                                precision, mean, s2, var, idx, st, ws)
     torch.cuda.synchronize()
     idx2 = idx.cpu().numpy()
     assert np.array_equal(idx2, g["idx"])
     for t in range(0, T, 4):  # stage-2 designs: the greedy path at theta = the estimate
         wt = dataclasses.replace(w, d=float(th1[t]))
-        info = check_location(wt, t, cand[t], idx2[t], mean[t].item(), s2[t].item(), "alc")
+        info = check_location(wt, t, cand[t], idx2[t], mean[t].item(), s2[t].item(), method)
         assert info["ok_vals"], info
     th2, _, st2 = gpu_mle(w, idx2, th1, tmin, tmax)
     assert np.array_equal(th2, g["theta"])
