@@ -1,26 +1,12 @@
 // predict.cu -- kernel (c) for a screen that returns only the local design: the FP64
-// predictive equations on the selected design of every location.
-//
-// Gramacy & Apley, Sec. 2, Eqs. predgp and preds2: with K_n = K(X_n, X_n) + g I,
-// k(x) = K(X_n, x) and psi = Y^T K_n^{-1} Y,
-//   mu(x) = k(x)^T K_n^{-1} Y,   s2(x) = psi (K(x, x) + g - k(x)^T K_n^{-1} k(x)) / n,
-// and var = psi (K(x, x) + g - k(x)^T K_n^{-1} k(x)) / (n - 2), the variance of the
-// Student-t predictive.  [K_n | k(x) | Y] is factored by a right-looking Cholesky, which
-// makes for every entry the same subtractions, in the same order, as the row-by-row
-// factorisation followed by forward substitution (u_x = L^{-1} k(x), y~ = L^{-1} Y):
-// v_n(x) = 1 + g - |u_x|^2 is a cancellation whose rounding error is of the order of the
-// tolerance, and keeping the textbook operation order keeps this kernel's rounding close
-// to that of a plain sequential evaluation.
-// The factorisation is fp64_chol.cuh's, flattened over the CTA's threads.
+// predictive equations (Sec. 2, Eqs. predgp and preds2) on the selected design of every
+// location, with the per-location arithmetic of predict_loc.cuh.
 //
 // One CTA owns one location at a time (persistent CTAs over a work queue); the matrix
 // lives in shared memory when it fits, else in a per-CTA slot of the workspace.
 #include <math.h>
 
-#include "batch.cuh"
-#include "fp64_chol.cuh"
-#include "fp64_exp.cuh"
-#include "internal.h"
+#include "predict_loc.cuh"
 
 namespace lagp {
 namespace {
@@ -44,16 +30,6 @@ struct PredParams {
   int *queue;
 };
 
-__device__ __forceinline__ double corr(const double *a, const double *b, int p, double theta_inv,
-                                       const double *etab) {
-  double acc = 0.0;
-  for (int k = 0; k < p; k++) {
-    const double t = a[k] - b[k];
-    acc = fma(t, t, acc);
-  }
-  return exp_nonpos(-acc * theta_inv, etab);
-}
-
 __global__ void __launch_bounds__(PB) predict_fp64_kernel(PredParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nmax = P.nmax;
@@ -72,52 +48,9 @@ __global__ void __launch_bounds__(PB) predict_fp64_kernel(PredParams P) {
     if (sh_loc >= P.T) break;
     const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, 0, 0, P.theta, P.g,
                                     P.idx, const_cast<int32_t *>(P.idx));
-    const int64_t loc = L.loc;
-    const int n = L.n, p = L.p, lda = n + 2;
-    const int32_t *d = L.idx;  // design indices of this location
-    if (tid < p) xl[tid] = L.x[tid];
-    if (tid == 0) sh_fail = d[0] < 0;  // the screen failed for this location
-    __syncthreads();
-    if (!sh_fail) {
-      // K_n + g I (lower triangle), k(x) and Y
-      const int ntri = n * (n + 1) / 2;
-      for (int e = tid; e < ntri + 2 * n; e += PB) {
-        if (e < ntri) {
-          const int a = tri_row(e), b = e - a * (a + 1) / 2;
-          const double *xa = L.X + (int64_t)d[a] * p;
-          A[a * lda + b] = (a == b) ? L.onepg
-                                    : corr(xa, L.X + (int64_t)d[b] * p, p, L.theta_inv, etab);
-        } else {
-          const int a = (e - ntri) >> 1, col = (e - ntri) & 1;
-          A[a * lda + n + col] = col == 0 ? corr(L.X + (int64_t)d[a] * p, xl, p, L.theta_inv, etab)
-                                          : L.Z[d[a]];
-        }
-      }
-      chol_flat_fp64(A, n, lda, 2, rl, &sh_fail);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      if (sh_fail) {
-        P.mean[loc] = NAN;
-        P.s2[loc] = NAN;
-        if (P.var) P.var[loc] = NAN;
-        if (P.status) P.status[loc] = (int8_t)LAGP_ERR_NOT_PD;
-      } else {
-        // in index order, as a sequential evaluation of the sums
-        double mu = 0.0, psi = 0.0, vx = L.onepg;
-        for (int i = 0; i < n; i++) {
-          const double ux = A[i * lda + n], yt = A[i * lda + n + 1];
-          mu = fma(ux, yt, mu);
-          psi = fma(yt, yt, psi);
-          vx = fma(-ux, ux, vx);
-        }
-        const double pv = psi * vx;
-        P.mean[loc] = mu;
-        P.s2[loc] = pv / n;
-        if (P.var) P.var[loc] = pv / (n - 2);
-        if (P.status) P.status[loc] = 0;
-      }
-    }
+    if (tid < L.p) xl[tid] = L.x[tid];
+    predict_location(L, L.idx, L.n, xl, A, rl, etab, &sh_fail, L.loc, P.mean, P.s2, P.var,
+                     P.status);
   }
 }
 

@@ -27,6 +27,7 @@
 
 #include "batch.cuh"
 #include "mixed_screen.cuh"
+#include "predict_loc.cuh"
 
 namespace lagp {
 namespace {
@@ -54,6 +55,9 @@ struct MixParams {
   int nstart;
   double r_min;          // > 1: stopping rule of Sec. 6; 0: the design has n points
   int32_t *n_out;        // design sizes (T) when r_min > 1
+  double *mean, *s2, *var;
+  int8_t *status;
+  int fuse_pred;         // 1: the predictive equations here (matrix in shared memory)
 };
 
 #ifndef LAGP_MIX_MINB
@@ -238,6 +242,20 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
     // evaluates the predictive equations on it in FP64
     for (int i = tid; i < n; i += MB) L.idx[i] = (sh_fail || i >= ne) ? -1 : cnd[dr[i]];
     if (P.n_out && tid == 0) P.n_out[L.loc] = sh_fail ? 0 : ne;
+    // The predictive equations on the design (kernel (c)'s arithmetic, predict_loc.cuh),
+    // here while the other resident CTAs screen -- FP64 work beside their FP32 work -- when
+    // the matrix fits in the shared-memory factor rows (dead now); the reciprocal pivots go
+    // to the per-warp row copies.  Otherwise kernel (c) runs after this kernel.  Only
+    // the instance without the row ring carries this code (in the other it costs 2 % on
+    // the 8-d workload, which has no room for the matrix anyway).
+    if constexpr (RA == 0) {
+      if (P.fuse_pred) {
+        __syncthreads();  // every thread reads the design below
+        predict_location(L, L.idx, sh_fail ? n : ne, xl, reinterpret_cast<double *>(Us),
+                         reinterpret_cast<double *>(wrow4), etab, &sh_fail, L.loc, P.mean, P.s2,
+                         P.var, P.status);
+      }
+    }
     // The factor rows in global memory are dead now (the next location rewrites each row
     // before reading it): drop their L2 lines without writing them back to DRAM.
     {
@@ -321,9 +339,12 @@ MixLayout mix_layout(int G, int p, int n, int M, int64_t T, int64_t idx_total, i
   return L;
 }
 
-// The screen, then kernel (c) on the designs it selected.
-int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, char *w,
-            int32_t *user_idx, const DevInfo &di, cudaStream_t stream) {
+// The screen and, per location, the predictive equations on the design it selected: in
+// the same kernel when the matrix fits in its shared memory (paper-2d: 14.43 -> 14.29 ms),
+// else by kernel (c) afterwards (the 8-d workload's n = 100: 139.5 ms either way in its
+// own kernel, 145.5 ms inside the screen from global memory).
+int mix_run(MixParams P, const MixLayout &L, int G, char *w, int32_t *user_idx,
+            const DevInfo &di, cudaStream_t stream) {
   P.queue = reinterpret_cast<int *>(w);
   P.rescores = reinterpret_cast<int *>(w + 256);
   char *o = w + 512;
@@ -338,6 +359,8 @@ int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, ch
   o += L.idx;
   const int RA = mix_ring_stages(P.Mpad, P.nmax, P.M, di);
   P.R = mix_rows_in_smem(P.Mpad, P.nmax, RA, di);
+  P.fuse_pred = RA == 0 && (size_t)P.R * P.Qpad * sizeof(float4) >=
+                              (size_t)P.nmax * (P.nmax + 2) * sizeof(double);
   const size_t smem = mix_smem_bytes(P.Mpad, P.nmax, P.R, RA);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
   cudaError_t e = RA ? cudaFuncSetAttribute(select_mixed_kernel<RING_A>,
@@ -353,10 +376,12 @@ int mix_run(MixParams P, const PredictArgs &pa_in, const MixLayout &L, int G, ch
     select_mixed_kernel<0><<<G, MB, smem, stream>>>(P);
   g_launches.fetch_add(1);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_status(e);
-  PredictArgs pa = pa_in;
-  pa.idx = P.idx;
+  if (e != cudaSuccess || P.fuse_pred) return cuda_status(e);
+  PredictArgs pa;
+  pa.X = P.X; pa.Z = P.Z; pa.p = P.pmax; pa.XX = P.XX; pa.T = P.T; pa.n = P.n; pa.nmax = P.nmax;
+  pa.theta = P.theta; pa.g = P.g; pa.idx = P.idx; pa.B = P.B;
   pa.B.n_loc = P.n_out;  // adaptive designs: kernel (c) on each location's own size
+  pa.mean = P.mean; pa.s2 = P.s2; pa.var = P.var; pa.status = P.status;
   return predict_fp64_launch(pa, o, L.pred, stream);
 }
 
@@ -384,11 +409,8 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   P.B = BatchView{nullptr, nullptr, nullptr, 0, a.theta_loc, nullptr};
   P.start = a.start; P.nstart = a.nstart;
   P.r_min = a.r_min; P.n_out = a.n_out;
-  PredictArgs pa;
-  pa.X = a.X; pa.Z = a.Z; pa.p = a.p; pa.XX = a.XX; pa.T = a.T; pa.n = a.n; pa.nmax = a.n;
-  pa.theta = a.theta; pa.g = a.g; pa.idx = nullptr; pa.B = P.B;
-  pa.mean = a.mean; pa.s2 = a.s2; pa.var = a.var; pa.status = a.status;
-  return mix_run(P, pa, L, G, static_cast<char *>(ws), a.idx, di, stream);
+  P.mean = a.mean; P.s2 = a.s2; P.var = a.var; P.status = a.status;
+  return mix_run(P, L, G, static_cast<char *>(ws), a.idx, di, stream);
 }
 
 size_t select_mixed_batch_workspace_bytes(const BatchLaunch &b, int G) {
@@ -414,11 +436,8 @@ int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, i
   P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr, nullptr};
   P.start = nullptr; P.nstart = 0;
   P.r_min = 0.0; P.n_out = nullptr;
-  PredictArgs pa;
-  pa.X = nullptr; pa.Z = nullptr; pa.p = b.pmax; pa.XX = b.XX; pa.T = b.T; pa.n = b.nmax;
-  pa.nmax = b.nmax; pa.theta = 1.0; pa.g = 0.0; pa.idx = nullptr; pa.B = P.B;
-  pa.mean = b.mean; pa.s2 = b.s2; pa.var = b.var; pa.status = b.status;
-  return mix_run(P, pa, L, G, static_cast<char *>(ws), b.idx, di, stream);
+  P.mean = b.mean; P.s2 = b.s2; P.var = b.var; P.status = b.status;
+  return mix_run(P, L, G, static_cast<char *>(ws), b.idx, di, stream);
 }
 
 int select_mixed_prepare() {
