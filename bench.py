@@ -38,13 +38,20 @@ EXP_FLOPS = 20      # FP64 flops counted per double-precision exp (see the design doc
 
 
 def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources: DRAM counters recorded for another revision are stale."""
+    """sha256 over the CUDA sources with their comments and blank space removed: DRAM
+    counters recorded for another revision of the code are stale (the sources hold no
+    string literal with a comment marker)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1303_0383_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
+        src = open(os.path.join(csrc, fn), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(" ".join(line.split()) for line in src.splitlines() if line.strip())
         h.update(fn.encode())
-        h.update(open(os.path.join(csrc, fn), "rb").read())
+        h.update(code.encode())
     return h.hexdigest()
 
 

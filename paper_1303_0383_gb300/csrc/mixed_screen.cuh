@@ -1,5 +1,7 @@
-// mixed_screen.cuh -- device code of the mixed-precision screen (select_mixed.cu): the
-// float-float exp, the per-pair step, score tracking and the FP64 re-score.
+// mixed_screen.cuh -- device code of the mixed-precision screens: the float-float exp, the
+// asynchronous row copies and L2 policies, the ALC per-pair step, score tracking and the
+// ALC FP64 re-score (select_mixed.cu; the MSPE kernel, select_mspe_mixed.cu, uses the
+// first parts).
 //
 // Gramacy & Apley, Sec. 3: the greedy local design adds the candidate that maximises the
 // ALC reduction cov_j(x,c)^2 / v_j(c) (Eq. dxy; SM Eq. dxy2); Sec. 3.2 gives the O(j)

@@ -19,10 +19,11 @@
 // step needs one block barrier: every thread merges the per-warp best/second-best results
 // and derives the step's pivot scalars itself.
 //
-// The kernel returns the selected design of every location; the predictive equations
-// (Eqs. predgp, preds2) are then evaluated in FP64 on that design by kernel (c) in
-// predict.cu, so mu, s2 and V carry FP64 accuracy whatever precision screened the
-// candidates.
+// The predictive equations (Eqs. predgp, preds2) are evaluated in FP64 on each selected
+// design with kernel (c)'s arithmetic (predict_loc.cuh) -- by this kernel itself right
+// after the design when the matrix fits in its shared memory, else by kernel (c) in
+// predict.cu afterwards -- so mu, s2 and V carry FP64 accuracy whatever precision
+// screened the candidates.
 #include <math.h>
 
 #include "batch.cuh"
