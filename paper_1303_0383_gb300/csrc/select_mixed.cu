@@ -64,18 +64,22 @@ struct MixParams {
 #ifndef LAGP_MIX_MINB
 #define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM, each with its first factor rows in shared memory
 #endif
-template <int RA>
+// RA: stages of the row ring (0: none).  SR: one shared copy of the step's factor row for
+// the whole CTA (one more block barrier per step) instead of one per warp, which frees
+// (MB/32 - 1) row copies of shared memory for the ring on large designs.
+template <int RA, bool SR>
 __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, nmax = P.nmax;
+  constexpr int NW = SR ? 1 : MB / 32;                       // copies of the factor row
   float4 *vp = reinterpret_cast<float4 *>(smraw);            // Qpad: v_j(c) pairs
   float4 *cp = vp + Qpad;                                    // Qpad: cov_j(x, c) pairs
-  // per-warp copies of the new factor row: {h, h, -h, -h} and {l, l} per entry
+  // copies of the new factor row: {h, h, -h, -h} and {l, l} per entry
   const int nrow = (nmax + 1) & ~1;
-  float4 *wrow4 = reinterpret_cast<float4 *>(cp + Qpad);     // (MB/32) x nrow
-  float2 *wrow2 = reinterpret_cast<float2 *>(wrow4 + (MB / 32) * nrow);  // (MB/32) x nrow
-  float2 *wxs = wrow2 + (MB / 32) * nrow;                    // (MB/32) x kMaxP: new point
-  int *dr = reinterpret_cast<int *>(wxs + (MB / 32) * kMaxP);  // nmax (padded to 4)
+  float4 *wrow4 = reinterpret_cast<float4 *>(cp + Qpad);     // NW x nrow
+  float2 *wrow2 = reinterpret_cast<float2 *>(wrow4 + NW * nrow);  // NW x nrow
+  float2 *wxs = wrow2 + NW * nrow;                           // NW x kMaxP: new point
+  int *dr = reinterpret_cast<int *>(wxs + NW * kMaxP);       // nmax (padded to 4)
   int *rlist = dr + ((nmax + 3) & ~3);                       // RESCORE_CAP
   unsigned char *used = reinterpret_cast<unsigned char *>(rlist + RESCORE_CAP);  // Mpad
   float4 *Us = reinterpret_cast<float4 *>(used + P.Mpad);    // R x Qpad: first factor rows
@@ -99,9 +103,9 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
   float4 *Xr = P.Xr + (size_t)blockIdx.x * P.pmax * Qpad;
   const int lda = nmax + 2;
   double *A = P.A + (size_t)blockIdx.x * nmax * lda;
-  float4 *srow4 = wrow4 + warp * nrow;  // this warp's copy of the new factor row
-  float2 *srow2 = wrow2 + warp * nrow;
-  float2 *sxs = wxs + warp * kMaxP;     // and of the new point's coordinates
+  float4 *srow4 = wrow4 + (SR ? 0 : warp) * nrow;  // this warp's copy of the new factor row
+  float2 *srow2 = wrow2 + (SR ? 0 : warp) * nrow;
+  float2 *sxs = wxs + (SR ? 0 : warp) * kMaxP;     // and of the new point's coordinates
 
   for (;;) {
     __syncthreads();
@@ -183,17 +187,24 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       }
       if (tid == 0) dr[j] = s;
       if (tid == ((s >> 1) % MB)) used[s] = 1;  // the pair's owner keeps the flags
-      // this warp's copy of the new factor row u_s and of x_s (relative to x)
-      for (int i = lane; i < j; i += 32) {
-        const ff u = ff2_get((i < R ? Us : U) + (size_t)i * Qpad, s);
-        srow4[i] = make_float4(u.h, u.h, -u.h, -u.h);
-        srow2[i] = f2s(u.l);
+      // this warp's (or the CTA's) copy of the new factor row u_s and of x_s (relative to x)
+      {
+        const int i0 = SR ? tid : lane, st = SR ? MB : 32;
+        for (int i = i0; i < j; i += st) {
+          const ff u = ff2_get((i < R ? Us : U) + (size_t)i * Qpad, s);
+          srow4[i] = make_float4(u.h, u.h, -u.h, -u.h);
+          srow2[i] = f2s(u.l);
+        }
+        if (i0 < p) {
+          const ff xk = ff2_get(Xr + i0 * Qpad, s);
+          sxs[i0] = make_float2(xk.h, xk.l);
+        }
       }
-      if (lane < p) {
-        const ff xk = ff2_get(Xr + lane * Qpad, s);
-        sxs[lane] = make_float2(xk.h, xk.l);
+      if constexpr (SR) {
+        __syncthreads();
+      } else {
+        __syncwarp();
       }
-      __syncwarp();
       if (j == n - 1) break;
       const bool want = j + 1 >= n0e;
       const ff2 inv2{f2s(inv.h), f2s(inv.l)}, uxj2{f2s(uxj.h), f2s(uxj.l)};
@@ -278,44 +289,63 @@ int mix_mpad(int M) { return (int)align_up((size_t)M, 64); }
 
 // Dynamic shared memory: the per-candidate state, then the first R factor rows and the
 // threads' row rings (RA stages).  Mpad is a multiple of 64, so the rows start 16-byte aligned.
-size_t mix_smem_bytes(int Mpad, int n, int R, int RA) {
+size_t mix_smem_bytes(int Mpad, int n, int R, int RA, bool SR) {
   const size_t Qpad = (size_t)Mpad / 2;
   const size_t nrow = (size_t)((n + 1) & ~1);
+  const size_t nw = SR ? 1 : MB / 32;
   return Qpad * 2 * sizeof(float4) +
-         (size_t)(MB / 32) * (nrow * (sizeof(float4) + sizeof(float2)) + kMaxP * sizeof(float2)) +
+         nw * (nrow * (sizeof(float4) + sizeof(float2)) + kMaxP * sizeof(float2)) +
          (size_t)((n + 3) & ~3) * sizeof(int) + RESCORE_CAP * sizeof(int) + (size_t)Mpad +
          (size_t)R * Qpad * sizeof(float4) + (size_t)RA * MB * sizeof(float4);
 }
 
 
 
-// Factor rows kept in shared memory: as many as LAGP_MIX_MINB resident CTAs per SM leave
-// room for (the rest stream from L2).  Row i is read at every step after step i, so the
-// first rows carry the most traffic.
-size_t mix_static_smem(int RA) {
+// The kernel instance of a launch: ring stages RA (0 or RING_A) and a shared factor-row
+// copy SR.
+struct MixVariant {
+  int RA;
+  bool SR;
+};
+
+const void *mix_kernel(MixVariant v) {
+  if (!v.RA) return reinterpret_cast<const void *>(select_mixed_kernel<0, false>);
+  return v.SR ? reinterpret_cast<const void *>(select_mixed_kernel<RING_A, true>)
+              : reinterpret_cast<const void *>(select_mixed_kernel<RING_A, false>);
+}
+
+size_t mix_static_smem(MixVariant v) {
   cudaFuncAttributes fa;
-  const cudaError_t e = RA ? cudaFuncGetAttributes(&fa, select_mixed_kernel<RING_A>)
-                           : cudaFuncGetAttributes(&fa, select_mixed_kernel<0>);
-  return e == cudaSuccess ? fa.sharedSizeBytes : 4096;
+  return cudaFuncGetAttributes(&fa, mix_kernel(v)) == cudaSuccess ? fa.sharedSizeBytes : 4096;
+}
+
+size_t mix_resident(int Mpad, int n, MixVariant v, const DevInfo &di) {
+  const size_t per = mix_static_smem(v) + 1024 + mix_smem_bytes(Mpad, n, 0, v.RA, v.SR);
+  const size_t k = di.smem_per_sm / per;  // 1 KB reserved per CTA
+  return k < (size_t)LAGP_MIX_MINB ? k : (size_t)LAGP_MIX_MINB;
 }
 
 // The row ring is used where a CTA's factor rows (n x M float-float entries) come mostly
 // from DRAM -- 8-d workload (n = 100, M = 2000) yes, paper-2d (n = 50, M = 1000) no, both
-// measured -- and only if its shared memory leaves as many CTAs resident per SM.
-int mix_ring_stages(int Mpad, int n, int M, const DevInfo &di) {
-  if ((int64_t)n * M < 100000) return 0;
-  auto resident = [&](int RA) {
-    const size_t per = mix_static_smem(RA) + 1024 + mix_smem_bytes(Mpad, n, 0, RA);
-    const size_t k = di.smem_per_sm / per;
-    return k < (size_t)LAGP_MIX_MINB ? k : (size_t)LAGP_MIX_MINB;
-  };
-  return resident(RING_A) >= resident(0) ? RING_A : 0;
+// measured -- and only if its shared memory leaves as many CTAs resident per SM; where the
+// per-warp row copies are what leave no room (large n, the batched workload), with one
+// shared copy.
+MixVariant mix_variant(int Mpad, int n, int M, const DevInfo &di) {
+  const MixVariant plain{0, false}, ring{RING_A, false}, ring_sr{RING_A, true};
+  if ((int64_t)n * M < 100000) return plain;
+  const size_t k0 = mix_resident(Mpad, n, plain, di);
+  if (mix_resident(Mpad, n, ring, di) >= k0) return ring;
+  if (mix_resident(Mpad, n, ring_sr, di) >= k0) return ring_sr;
+  return plain;
 }
 
-int mix_rows_in_smem(int Mpad, int n, int RA, const DevInfo &di) {
-  const size_t stat = mix_static_smem(RA);
+// Factor rows kept in shared memory: as many as LAGP_MIX_MINB resident CTAs per SM leave
+// room for (the rest stream from L2).  Row i is read at every step after step i, so the
+// first rows carry the most traffic.
+int mix_rows_in_smem(int Mpad, int n, MixVariant v, const DevInfo &di) {
+  const size_t stat = mix_static_smem(v);
   size_t per_cta = di.smem_per_sm / LAGP_MIX_MINB;
-  const size_t fixed = stat + 1024 + mix_smem_bytes(Mpad, n, 0, RA);  // 1 KB reserved per CTA
+  const size_t fixed = stat + 1024 + mix_smem_bytes(Mpad, n, 0, v.RA, v.SR);  // 1 KB reserved per CTA
   if (per_cta > di.smem_optin) per_cta = di.smem_optin;
   if (per_cta <= fixed) return 0;
   const size_t row = (size_t)Mpad / 2 * sizeof(float4);
@@ -358,23 +388,23 @@ int mix_run(MixParams P, const MixLayout &L, int G, char *w, int32_t *user_idx,
   // the design goes to the caller's idx, or to the workspace when the caller wants none
   P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(o);
   o += L.idx;
-  const int RA = mix_ring_stages(P.Mpad, P.nmax, P.M, di);
-  P.R = mix_rows_in_smem(P.Mpad, P.nmax, RA, di);
-  P.fuse_pred = RA == 0 && (size_t)P.R * P.Qpad * sizeof(float4) >=
-                              (size_t)P.nmax * (P.nmax + 2) * sizeof(double);
-  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax, P.R, RA);
+  const MixVariant v = mix_variant(P.Mpad, P.nmax, P.M, di);
+  P.R = mix_rows_in_smem(P.Mpad, P.nmax, v, di);
+  P.fuse_pred = v.RA == 0 && (size_t)P.R * P.Qpad * sizeof(float4) >=
+                                 (size_t)P.nmax * (P.nmax + 2) * sizeof(double);
+  const size_t smem = mix_smem_bytes(P.Mpad, P.nmax, P.R, v.RA, v.SR);
   if (smem > di.smem_optin) return LAGP_ERR_INVALID_ARG;
-  cudaError_t e = RA ? cudaFuncSetAttribute(select_mixed_kernel<RING_A>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                     : cudaFuncSetAttribute(select_mixed_kernel<0>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(mix_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaMemsetAsync(w, 0, 512, stream);  // work counter and re-score counter
   if (e != cudaSuccess) return cuda_status(e);
-  if (RA)
-    select_mixed_kernel<RING_A><<<G, MB, smem, stream>>>(P);
+  if (!v.RA)
+    select_mixed_kernel<0, false><<<G, MB, smem, stream>>>(P);
+  else if (v.SR)
+    select_mixed_kernel<RING_A, true><<<G, MB, smem, stream>>>(P);
   else
-    select_mixed_kernel<0><<<G, MB, smem, stream>>>(P);
+    select_mixed_kernel<RING_A, false><<<G, MB, smem, stream>>>(P);
   g_launches.fetch_add(1);
   e = cudaGetLastError();
   if (e != cudaSuccess || P.fuse_pred) return cuda_status(e);
