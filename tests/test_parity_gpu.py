@@ -323,3 +323,11 @@ def test_largest_design_and_candidate_count_run(method):
     same = (f["idx"] == m["idx"]).all(axis=1)
     rel = np.abs(f["s2"][same] - m["s2"][same]) / f["s2"][same]
     assert same.any() and rel.max() <= 1e-9, (same, rel)
+
+
+def test_mixed_shared_factor_row_instance_parity():
+    # n = 180 with 4000 candidates: the per-warp copies of the factor row would leave no
+    # room for the row ring, so the mixed kernel runs its instance with one shared copy
+    w = inputs.random_case(33, 9000, 2, 2, 6, 180, 4000, d=0.2)
+    g, infos, bad = run_parity(w, precision="mixed")
+    assert not bad, bad[:3]
