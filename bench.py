@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "local-GP predictions/sec (n=50, 1000 cand) FP64 plain vs mixed; serving p99 ms"
 UNIT = "predictions/s"
 FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 flop x max clock
-EXP_FLOPS = 20      # FP64 flops counted per double-precision exp
+EXP_FLOPS = 20      # FP64 flops counted per double-precision exp (measured: about 20 DFMA each)
 
 
 def kernel_source_hash() -> str:
