@@ -44,3 +44,12 @@ def test_generators_are_deterministic():
     assert np.array_equal(a.X, b.X) and np.array_equal(a.Z, b.Z)
     c, d = inputs.paper_2d(), inputs.paper_2d()
     assert np.array_equal(c.XX, d.XX) and np.array_equal(c.Z, d.Z)
+
+
+def test_borehole_domain_is_the_papers():
+    # the eight input ranges printed below Eq. borehole (tests/golden/borehole_domain.txt)
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "borehole_domain.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert [r[0] for r in rows] == ["r_w", "r", "T_u", "T_l", "H_u", "H_l", "L", "K_w"]
+    assert [(float(r[1]), float(r[2])) for r in rows] == [tuple(map(float, b)) for b in inputs.BOREHOLE_BOX]
