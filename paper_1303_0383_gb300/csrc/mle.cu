@@ -36,6 +36,7 @@ namespace {
 
 constexpr int LB = 256;                      // threads per CTA
 constexpr size_t kSmemMle = 110 * 1024;      // largest per-CTA set kept in shared memory
+constexpr int kSums = 7;                     // block sums per Newton iteration
 
 struct MleParams {
   const double *X, *Z;
@@ -66,15 +67,10 @@ size_t mle_set_bytes(int n) {
   return nn * 3 * sizeof(double) + (size_t)n * (4 + kMaxP) * sizeof(double);
 }
 
-__device__ double block_sum(double v, double *red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Lane 0's shuffle-tree sum of v over its warp.
+__device__ __forceinline__ double warp_tree_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < LB / 32; w++) s += red[w];
-  return s;
+  return v;
 }
 
 __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
@@ -88,7 +84,7 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
   double *Y = Ki + nn, *w = Y + nmax, *kdw = w + nmax, *rl = kdw + nmax;
   double *xd = rl + nmax;    // nmax x p coordinates of the design
   __shared__ double etab[64];
-  __shared__ double red[LB / 32];
+  __shared__ double red[kSums][LB / 32];
   __shared__ double sh_th, sh_lo, sh_hi;
   __shared__ int sh_loc, sh_fail, sh_done, sh_lo_open, sh_hi_open, sh_it, sh_st;
   const int tid = threadIdx.x;
@@ -224,10 +220,10 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
         Kdf[e] = make_float2(kd.h, kd.l);
       }
       __syncthreads();
-      double t2p = 0.0;
-      for (int e = tid; e < n * n; e += LB) {  // each (a <= b) pair forms A_ab and A_ba
-        const int a = e / n, b = e % n;
-        if (b < a) continue;
+      // The pairs a <= b, all lanes busy: (a == b ? 1 : 2) A_ab into slot (a, b) and A_ba into
+      // slot (b, a) of the dead L^-1 storage (for a == b both are A_aa, in one slot).
+      for (int e = tid; e < ntri; e += LB) {
+        const int b = tri_row(e), a = e - b * (b + 1) / 2;
         ffacc sab{0.0f, 0.0f}, sba{0.0f, 0.0f};
         for (int m = 0; m < n; m++) {
           const float2 x1 = Kif[a * lda + m], y1 = Kdf[m * lda + b];
@@ -236,16 +232,49 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
           ffacc_add_prod(sba, ff{x2.x, x2.y}, ff{y2.x, y2.y});
         }
         const double vab = (double)sab.h + (double)sab.l, vba = (double)sba.h + (double)sba.l;
-        t2p = fma((a == b ? 1.0 : 2.0) * vab, vba, t2p);
+        Xb[a * lda + b] = (a == b ? 1.0 : 2.0) * vab;
+        if (a != b) Xb[b * lda + a] = vba;
       }
-      psi = block_sum(psi, red);
-      q3 = block_sum(q3, red);
-      q1 = block_sum(q1, red);
-      q2 = block_sum(q2, red);
-      t1 = block_sum(t1, red);
-      t3 = block_sum(t3, red);
-      const double t2 = block_sum(t2p, red);
+      __syncthreads();
+      // each thread adds its pairs in the order of the row-major (a, b) scan
+      double t2p = 0.0;
+      for (int e = tid; e < n * n; e += LB) {
+        const int a = e / n, b = e % n;
+        if (b < a) continue;
+        t2p = fma(Xb[a * lda + b], Xb[b * lda + a], t2p);
+      }
+      // The seven block sums: a shuffle tree per warp, then thread 0 adds the warp totals in
+      // warp order.  The six row sums are exactly +0.0 in warps that hold no row (tid >= n),
+      // whose tree would give +0.0, so those warps skip it.
+      {
+        const int lane = tid & 31, warp = tid >> 5;
+        double v[kSums] = {psi, q3, q1, q2, t1, t3, t2p};
+        if (warp * 32 < n) {
+#pragma unroll
+          for (int j = 0; j < kSums - 1; j++) v[j] = warp_tree_sum(v[j]);
+        }
+        v[kSums - 1] = warp_tree_sum(v[kSums - 1]);
+        if (lane == 0) {
+#pragma unroll
+          for (int j = 0; j < kSums; j++) red[j][warp] = v[j];
+        }
+      }
+      __syncthreads();
       if (tid == 0) {
+        double v[kSums];
+#pragma unroll
+        for (int j = 0; j < kSums; j++) {
+          double s = 0.0;
+          for (int w = 0; w < LB / 32; w++) s += red[j][w];
+          v[j] = s;
+        }
+        psi = v[0];
+        q3 = v[1];
+        q1 = v[2];
+        q2 = v[3];
+        t1 = v[4];
+        t3 = v[5];
+        const double t2 = v[6];
         const double dn = n;
         const double d1 = -0.5 * t1 + dn / 2.0 * q3 / psi;
         const double d2 = -0.5 * (t3 - t2) + dn / (2.0 * psi) * (q1 - 2.0 * q2) +
