@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
       // x_ii = 1 / l_ii.  Right-looking: at step m every entry (i > m, c <= m) takes its
       // term l_im x_mc -- the same terms in the same order as the row-by-row sums -- and
       // the thread that adds the last term of row m + 1 finishes that entry, so a step is
-      // one barrier and all threads share its FP64 work.
+      // one barrier and all threads share its FP64 work.  Row m + 1 runs in a loop of its
+      // own: in the shared loop its multiply by 1 / l_ii would be a predicated FP64
+      // instruction issued by every warp.
       double *Xb = Ki;
       for (int e = tid; e < ntri; e += LB) {
         const int a = tri_row(e), b = e - a * (a + 1) / 2;
@@ -158,10 +160,14 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
       __syncthreads();
       for (int m = 0; m < n - 1; m++) {
         const int w1 = m + 1, cnt = (n - 1 - m) * w1;
-        for (int e = tid; e < cnt; e += LB) {
+        {  // row m + 1: its last term, then the division by its pivot
+          const int i = m + 1;
+          for (int c = tid; c < w1; c += LB)
+            Xb[i * lda + c] = -fma(Lm[i * lda + m], Xb[m * lda + c], Xb[i * lda + c]) * rl[i];
+        }
+        for (int e = w1 + tid; e < cnt; e += LB) {
           const int i = m + 1 + e / w1, c = e % w1;
-          const double sv = fma(Lm[i * lda + m], Xb[m * lda + c], Xb[i * lda + c]);
-          Xb[i * lda + c] = (i == m + 1) ? -sv * rl[i] : sv;
+          Xb[i * lda + c] = fma(Lm[i * lda + m], Xb[m * lda + c], Xb[i * lda + c]);
         }
         __syncthreads();
       }
