@@ -37,16 +37,38 @@ FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 fl
 EXP_FLOPS = 20      # FP64 flops counted per double-precision exp (measured: about 20 DFMA each)
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources with their comments and blank space removed: DRAM
-    counters recorded for another revision of the code are stale (the sources hold no
-    string literal with a comment marker)."""
+def kernel_source_hash(unit: str | None = None) -> str:
+    """sha256 over CUDA sources with their comments and blank space removed: DRAM counters
+    recorded for another revision of a kernel's code are stale (the sources hold no string
+    literal with a comment marker).  unit: a translation unit of the library (such as
+    "select_mixed.cu"), hashed with the local headers it includes, transitively; None:
+    every source of the library."""
     import hashlib
     import re
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1303_0383_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        src = open(os.path.join(csrc, fn), encoding="utf-8").read()
+    dirs = [os.path.join(ROOT, "paper_1303_0383_gb300", "csrc"), os.path.join(ROOT, "include")]
+
+    def find(fn):
+        for d in dirs:
+            if os.path.isfile(os.path.join(d, fn)):
+                return os.path.join(d, fn)
+        return None
+
+    if unit is None:
+        files = [(fn, os.path.join(dirs[0], fn)) for fn in sorted(os.listdir(dirs[0]))]
+    else:
+        seen, todo = {}, [unit]
+        while todo:
+            fn = todo.pop()
+            path = find(fn)
+            if fn in seen or path is None:
+                continue
+            seen[fn] = path
+            todo += re.findall(r'^\s*#\s*include\s+"([^"]+)"', open(path, encoding="utf-8").read(),
+                               flags=re.M)
+        files = sorted(seen.items())
+    for fn, path in files:
+        src = open(path, encoding="utf-8").read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
         code = "\n".join(" ".join(line.split()) for line in src.splitlines() if line.strip())
@@ -396,7 +418,8 @@ def stored_traffic(prec):
         return None
     try:
         for tj in json.load(open(tpath)).get("entries", []):
-            if tj.get("precision") == prec and tj.get("source_sha256") == kernel_source_hash():
+            if tj.get("precision") == prec and \
+                    tj.get("source_sha256") == kernel_source_hash(tj.get("unit")):
                 return tj.get("bytes_per_launch")
     except Exception:
         return None
