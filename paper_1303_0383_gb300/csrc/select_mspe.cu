@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
     const int n = L.n, p = L.p, M = L.M;
     const int32_t *cnd = L.cand;
     const double th = L.theta, th2 = th * th, th3 = th2 * th, th4 = th2 * th2;
+    const double ith2 = 1.0 / th2;
     if (tid < p) xl[tid] = L.x[tid];
     if (tid == 0) {
       sh_fail = 0;
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
       const int jn = j + 1;  // design size after this step
       const bool want = (jn >= n0e) && (jn >= 3);
       const double dj = (double)(jn - 2);
+      const double rdj = 1.0 / dj, pdj = psi / dj;
       double bs = INFINITY;
       int br = 0x7fffffff;
       for (int c = tid; c < limit; c += TB) {
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
           acc = fma(t, t, acc);
         }
         const double ksc = exp_nonpos(-acc * L.theta_inv, etab);
-        const double kdsc = ksc * acc / th2;
+        const double kdsc = ksc * acc * ith2;
         double d1 = ksc, d2 = kdsc, d3 = 0.0;
         const double *Uc = U + c, *Udc = Ud + c;
         for (int i = 0; i < j; i++, Uc += Mpad, Udc += Mpad) {
@@ -330,11 +332,15 @@ __global__ void __launch_bounds__(TB, 1) select_mspe_kernel(MspeParams P) {
         qc[c] = qn;
         mc[c] = mn;
         if (want && vc > 0.0) {
-          const double Vc = psi * vc / dj;
+          // two divisions, 1 / V_c and 1 / G: dVc^2 / (2 V_c^2) = (dVc / V_c)^2 / 2 and
+          // 1 / v_c = (psi / (j - 2)) / V_c
+          const double Vc = pdj * vc;
+          const double rV = 1.0 / Vc;
           const double dmuc = pc - mn;
-          const double dVc = (-wKdw * vc - psi * (2.0 * kz - qn)) / dj;
-          const double G = F + dVc * dVc / (2.0 * Vc * Vc) + dmuc * dmuc / Vc;
-          const double Jc = psi / dj * (vx - cx * cx / vc) + dmux * dmux / G;
+          const double dVc = (-wKdw * vc - psi * (2.0 * kz - qn)) * rdj;
+          const double dr = dVc * rV;
+          const double G = F + 0.5 * dr * dr + dmuc * dmuc * rV;
+          const double Jc = pdj * (vx - cx * cx * (pdj * rV)) + dmux * dmux / G;
           if (Jc == Jc && j_better(Jc, c, bs, br)) { bs = Jc; br = c; }
         }
       }
