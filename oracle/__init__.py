@@ -36,6 +36,14 @@ def _lib_path(long_double: bool) -> str:
     return os.path.join(_BUILD, "liblagp_oracle_ld.so" if long_double else "liblagp_oracle.so")
 
 
+def _gcc(src: str, out: str, long_double: bool) -> list:
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-Wl,-Bsymbolic", "-o", out, src, "-lm"]
+    if long_double:
+        cmd.insert(1, "-DLAGP_ORACLE_LONG")
+    return cmd
+
+
 def build(force: bool = False) -> None:
     """Compile both oracle libraries with gcc (FP64 and long double)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -43,46 +51,69 @@ def build(force: bool = False) -> None:
         out = _lib_path(ld)
         if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
             continue
-        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-fPIC", "-shared", "-Wl,-Bsymbolic", "-o", out + ".tmp", _SRC, "-lm"]
-        if ld:
-            cmd.insert(1, "-DLAGP_ORACLE_LONG")
-        subprocess.run(cmd, check=True)
+        subprocess.run(_gcc(_SRC, out + ".tmp", ld), check=True)
         os.replace(out + ".tmp", out)
+
+
+def build_variant(source: str, outdir: str) -> tuple:
+    """Compile another version of the oracle source (a test plants mistakes in a copy
+    this way) into outdir; returns the FP64 and long-double library paths.  Load them
+    with load_variant."""
+    os.makedirs(outdir, exist_ok=True)
+    src = os.path.join(outdir, "lagp_oracle_variant.c")
+    with open(src, "w") as f:
+        f.write(source)
+    outs = (os.path.join(outdir, "variant.so"), os.path.join(outdir, "variant_ld.so"))
+    procs = [subprocess.Popen(_gcc(src, o, ld), stderr=subprocess.PIPE)
+             for o, ld in zip(outs, (False, True))]
+    for pr in procs:
+        _, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("gcc failed on the variant: %s" % err.decode(errors="replace"))
+    return outs
+
+
+def load_variant(path: str):
+    """ctypes handle of a library built by build_variant, with the oracle's signatures."""
+    return _bind(ctypes.CDLL(path))
+
+
+def _bind(L):
+    """Declare the C signatures on a loaded oracle library."""
+    P = ctypes.c_void_p
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.orc_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
+    L.orc_local_design.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64, i32,
+                                   P, P, P, P, P, P]
+    L.orc_local_design_adaptive.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64,
+                                            f64, P, P, P, P, P, P, P]
+    L.orc_local_design_start.argtypes = [P, P, i64, i32, P, P, i32, P, i32, i32, f64, f64,
+                                         i32, P, P, P, P, P, P]
+    L.orc_predict.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32,
+                              P, P, P, P, P, P, i32]
+    L.orc_full_gp.argtypes = [P, P, i64, i32, P, f64, f64, P, P]
+    L.orc_design_predict.argtypes = [P, P, i64, i32, P, P, i32, f64, f64, P]
+    L.orc_chol.argtypes = [P, i32, P]
+    L.orc_inverse.argtypes = [P, i32, P]
+    L.orc_pinv_update.argtypes = [P, i32, P, f64, P]
+    L.orc_loglik.argtypes = [P, P, i32, i32, f64, f64, P]
+    L.orc_pred_derivs.argtypes = [P, P, i32, i32, P, f64, f64, P]
+    L.orc_d2l_conditional.argtypes = [P, f64, i32]
+    L.orc_d2l_conditional.restype = f64
+    L.orc_alc_forms.argtypes = [P, i32, i32, P, P, f64, f64, P]
+    L.orc_corr.argtypes = [P, P, i32, f64]
+    L.orc_corr.restype = f64
+    L.orc_mle.argtypes = [P, P, i64, i32, P, i32, f64, f64, f64, f64, i32, f64, P, P]
+    L.orc_mle_batch.argtypes = [P, P, i64, i32, i64, P, i32, P, f64, f64, f64, i32, f64,
+                                P, P, P, i32]
+    return L
 
 
 def _lib(long_double: bool = False):
     with _lock:
         if long_double not in _libs:
             build()
-            L = ctypes.CDLL(_lib_path(long_double))
-            P = ctypes.c_void_p
-            i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
-            L.orc_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
-            L.orc_local_design.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64, i32,
-                                           P, P, P, P, P, P]
-            L.orc_local_design_adaptive.argtypes = [P, P, i64, i32, P, P, i32, i32, i32, f64, f64,
-                                                    f64, P, P, P, P, P, P, P]
-            L.orc_local_design_start.argtypes = [P, P, i64, i32, P, P, i32, P, i32, i32, f64, f64,
-                                                 i32, P, P, P, P, P, P]
-            L.orc_predict.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32,
-                                      P, P, P, P, P, P, i32]
-            L.orc_full_gp.argtypes = [P, P, i64, i32, P, f64, f64, P, P]
-            L.orc_design_predict.argtypes = [P, P, i64, i32, P, P, i32, f64, f64, P]
-            L.orc_chol.argtypes = [P, i32, P]
-            L.orc_inverse.argtypes = [P, i32, P]
-            L.orc_pinv_update.argtypes = [P, i32, P, f64, P]
-            L.orc_loglik.argtypes = [P, P, i32, i32, f64, f64, P]
-            L.orc_pred_derivs.argtypes = [P, P, i32, i32, P, f64, f64, P]
-            L.orc_d2l_conditional.argtypes = [P, f64, i32]
-            L.orc_d2l_conditional.restype = f64
-            L.orc_alc_forms.argtypes = [P, i32, i32, P, P, f64, f64, P]
-            L.orc_corr.argtypes = [P, P, i32, f64]
-            L.orc_corr.restype = f64
-            L.orc_mle.argtypes = [P, P, i64, i32, P, i32, f64, f64, f64, f64, i32, f64, P, P]
-            L.orc_mle_batch.argtypes = [P, P, i64, i32, i64, P, i32, P, f64, f64, f64, i32, f64,
-                                        P, P, P, i32]
-            _libs[long_double] = L
+            _libs[long_double] = _bind(ctypes.CDLL(_lib_path(long_double)))
         return _libs[long_double]
 
 

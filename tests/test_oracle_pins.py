@@ -336,7 +336,9 @@ def test_mspe_without_derivative_term_ranks_as_alc():
 def test_mspe_criterion_matches_finite_difference_assembly():
     """MSPE step on a tiny case: J(c) assembled from finite differences of the
     predictive mean/variance and of the log-likelihood (Eqs. mspe, newv, G; SM Ed2la)
-    picks the same candidate as the oracle's first MSPE step."""
+    picks the same candidate as the oracle's first MSPE step, and its best and
+    second-best values agree with the oracle's (the finite differences are accurate to
+    about 1e-7 here)."""
     w = inputs.random_case(41, 120, 2, 3, 5, 6, 30, d=0.3, g=1e-4)
     cand = oracle.knn(w.X, w.XX, w.ncand)
     for t in range(w.T):
@@ -354,7 +356,7 @@ def test_mspe_criterion_matches_finite_difference_assembly():
         dmu_x = (mv(Xd, Y, x, d + h)[0] - mv(Xd, Y, x, d - h)[0]) / (2 * h)
         F = -(np_loglik(Xd, Y, d + h, g) - 2 * np_loglik(Xd, Y, d, g) + np_loglik(Xd, Y, d - h, g)) / h ** 2
         _, _, _, psi = mv(Xd, Y, x, d)
-        best, bestJ = None, np.inf
+        best, bestJ, Js = None, np.inf, []
         for c in cand[t][w.n0:]:
             xc = w.X[c]
             mp, Vp, _, _ = mv(Xd, Y, xc, d + h)
@@ -364,9 +366,14 @@ def test_mspe_criterion_matches_finite_difference_assembly():
             G = F + dV_c ** 2 / (2 * Vc ** 2) + dmu_c ** 2 / Vc
             _, _, v1, _ = np_pred(np.vstack([Xd, xc]), np.ones(j + 1), x, d, g)
             J = psi / (j - 2) * v1 + dmu_x ** 2 / G
+            Js.append(J)
             if J < bestJ:
                 best, bestJ = c, J
         assert r["idx"][w.n0] == best, t
+        first, second = np.sort(Js)[:2]
+        tr = r["trace"][0]                  # best, best score, chosen, its score, second
+        assert abs(tr[1] - first) <= 1e-5 * abs(first), (t, tr[1], first)
+        assert abs(tr[4] - second) <= 1e-5 * abs(second), (t, tr[4], second)
 
 
 def test_long_double_oracle_agrees():
