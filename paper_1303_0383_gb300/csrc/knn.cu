@@ -7,7 +7,9 @@
 //
 // FP64 is 1/58 of FP32 throughput on this GPU, so exact distances are computed only for
 // the few points that can be members.  One CTA owns one location at a time:
-//   prep    (once per call) an FP32 copy of X and B = max |coordinate|;
+//   prep    (once per call) an FP32 copy of X, dimension-major (a warp's load of one
+//           coordinate of 32 consecutive points is one 128-byte line), and
+//           B = max |coordinate|;
 //   pass 1  FP32 squared distance d2f of every design point and a 4096-bin histogram of
 //           the top 12 bits of d2f (non-negative floats order like their bit patterns);
 //   select  a block scan finds the bin b* holding the ncand-th smallest d2f; tau is the
@@ -17,8 +19,9 @@
 //           fused sum; see fp32_err_bound) -- all true members survive; the survivors are
 //           listed in shared memory and then get their exact FP64 d2 from that list, so
 //           the FP64 work runs on full warps;
-//   sort    bitonic sort of the survivors by (d2 bits, index); the first ncand indices
-//           are written out.
+//   sort    the survivors in (d2, index) order: a bucket sort on d2 with insertion in the
+//           buckets, or a bitonic sort on (d2 bits, index) where buckets overflow; the
+//           first ncand indices are written out.
 // If the survivors do not fit in shared memory (many points tied at the boundary), the
 // CTA redoes that location exactly in FP64: a 4096-bin histogram of float(d2) over exact
 // d2 (recomputed in every pass: no scratch), and radix refinement on the 96-bit key (d2 bits, index) for an
@@ -225,13 +228,15 @@ __device__ int knn_exact_location(const double *__restrict__ X, int N, int p, in
   return (int)*sh_count;
 }
 
-__global__ void knn_prep_kernel(const double *__restrict__ X, int64_t n, float *__restrict__ Xf,
-                                unsigned int *__restrict__ bmax) {
+// The FP32 copy of X (N x p, row-major) in dimension-major order, and B = max |coordinate|.
+__global__ void knn_prep_kernel(const double *__restrict__ X, int64_t N, int p,
+                                float *__restrict__ Xf, unsigned int *__restrict__ bmax) {
   __shared__ unsigned int wmax[KB / 32];
   unsigned int m = 0;
+  const int64_t n = N * p;
   for (int64_t i = blockIdx.x * (int64_t)KB + threadIdx.x; i < n; i += (int64_t)gridDim.x * KB) {
     const double x = X[i];
-    Xf[i] = __double2float_rn(x);
+    Xf[(i % p) * N + i / p] = __double2float_rn(x);
     const float a = __double2float_ru(fabs(x));
     m = max(m, __float_as_uint(a));
   }
@@ -244,18 +249,21 @@ __global__ void knn_prep_kernel(const double *__restrict__ X, int64_t n, float *
   }
 }
 
+// FP32 d2 of point i; Xf is dimension-major (coordinate k of point i at Xf[k N + i]), so a
+// warp's load of one coordinate is one contiguous 128-byte line.
 template <int P>
-__device__ __forceinline__ float sqdist_f32(const float *xf, const float *xi, int p) {
+__device__ __forceinline__ float sqdist_f32(const float *xf, const float *__restrict__ Xf, int i,
+                                            int N, int p) {
   float acc = 0.0f;
   if (P > 0) {
 #pragma unroll
     for (int k = 0; k < P; k++) {
-      const float dk = __fsub_rn(xf[k], xi[k]);
+      const float dk = __fsub_rn(xf[k], Xf[(size_t)k * N + i]);
       acc = __fmaf_rn(dk, dk, acc);
     }
   } else {
     for (int k = 0; k < p; k++) {
-      const float dk = __fsub_rn(xf[k], xi[k]);
+      const float dk = __fsub_rn(xf[k], Xf[(size_t)k * N + i]);
       acc = __fmaf_rn(dk, dk, acc);
     }
   }
@@ -381,7 +389,7 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     __syncthreads();
     // pass 1: histogram of the FP32 distances
     for (int i = threadIdx.x; i < N; i += KB) {
-      const float d2f = sqdist_f32<P>(xf, Xf + (size_t)i * p, p);
+      const float d2f = sqdist_f32<P>(xf, Xf, i, N, p);
       atomicAdd(&hist[__float_as_uint(d2f) >> (31 - HBITS)], 1u);
     }
     __syncthreads();
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     const float thr = sh_thr;
     // pass 2: the same FP32 distances again (bit for bit); survivors are listed first
     for (int i = threadIdx.x; i < N; i += KB) {
-      const float d2f = sqdist_f32<P>(xf, Xf + (size_t)i * p, p);
+      const float d2f = sqdist_f32<P>(xf, Xf, i, N, p);
       if (d2f <= thr) {
         const uint32_t pos = atomicAdd(&sh_count, 1u);
         if (pos < (uint32_t)cap) sidx[pos] = i;
@@ -455,7 +463,7 @@ int knn_grid(int64_t T, int num_sms, size_t smem) {
 
 }  // namespace
 
-// Scratch layout: [bmax (256 B)] [Xf: N*p floats]
+// Scratch layout: [bmax (256 B)] [Xf: p x N floats, dimension-major]
 size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms) {
   (void)T;
   (void)ncand;
@@ -501,7 +509,7 @@ int knn_launch_list(const double *X, int64_t N, int32_t p, const double *XX, int
   const int64_t n = N * p;
   int pblocks = (int)((n + KB - 1) / KB);
   if (pblocks > 4 * di.num_sms) pblocks = 4 * di.num_sms;
-  knn_prep_kernel<<<pblocks, KB, 0, stream>>>(X, n, Xf, bmax);
+  knn_prep_kernel<<<pblocks, KB, 0, stream>>>(X, N, p, Xf, bmax);
   g_launches.fetch_add(1);
   const int Ni = (int)N;
   void *args[] = {(void *)&X, (void *)&Ni, (void *)&p, (void *)&XX, (void *)&nloc, (void *)&M,
