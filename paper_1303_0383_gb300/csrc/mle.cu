@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(LB) mle_fp64_kernel(MleParams P) {
         t2p = fma(Xb[a * lda + b], Xb[b * lda + a], t2p);
       }
       // The seven block sums: a shuffle tree per warp, then thread 0 adds the warp totals in
-      // warp order.  The six row sums are exactly +0.0 in warps that hold no row (tid >= n),
-      // whose tree would give +0.0, so those warps skip it.
+      // warp order.  The six row sums are exactly +0.0 in a warp none of whose threads holds
+      // a row (warp * 32 >= n), whose tree would give +0.0, so such warps skip it.
       {
         const int lane = tid & 31, warp = tid >> 5;
         double v[kSums] = {psi, q3, q1, q2, t1, t3, t2p};
