@@ -95,6 +95,15 @@ MUTANTS = [
     ("stopping rule ratio v_j(x) / score instead of v_j(x) / v_{j+1}(x)",
      "vx / (vx - chosen_s)",
      "vx / chosen_s"),
+    ("stopping rule stops where the ratio is above r_min",
+     "if (r_min > 0 && !forced && ratio < r_min) {",
+     "if (r_min > 0 && !forced && ratio > r_min) {"),
+    ("saved start design accepted with a repeated point",
+     "if (r < 0 || W->used[r]) return LAGP_ORC_INVALID;",
+     "if (r < 0) return LAGP_ORC_INVALID;"),
+    ("predictions on a given design: s2 divided by n - 2",
+     "out[1] = (double)(psi * v / n);",
+     "out[1] = (double)(psi * v / (n - 2));"),
 ]
 
 
