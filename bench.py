@@ -148,8 +148,9 @@ def mspe_flops_per_location(n0, n, M, p):
 
 
 # The single-design workloads: generator, the (method, precision) variants timed, the
-# headline variant, the CPU-oracle sample size (about 10-30 s of work on 16 cores) and the
-# paper's own rate for the same problem where it gives one.
+# headline variant, the CPU-oracle sample size (about 10-30 s of work on 16 cores), the
+# untimed oracle sample for the accuracy of another method's variants, and the paper's own
+# rate for the same problem where it gives one.
 def _workloads():
     from paper_1303_0383_gb300 import inputs
     return {
@@ -157,7 +158,7 @@ def _workloads():
                          head=("alc", "mixed"), cpu=1600, paper=None),
         "smooth-8d": dict(make=inputs.smooth_8d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"),
                                                             ("mspe", "mixed")],
-                          head=("alc", "mixed"), cpu=120, paper=None),
+                          head=("alc", "mixed"), cpu=120, acc_other=64, paper=None),
         "grid-2d": dict(make=inputs.grid_2d, variants=[("alc", "fp64"), ("alc", "mixed"), ("mspe", "fp64"), ("mspe", "mixed"), ("nn", "fp64")],
                         head=("alc", "mixed"), cpu=1600,
                         paper={"value": 10000 / 30.0, "what": "Sec. 4.1: about 30 s for 10K locations, "
@@ -235,7 +236,9 @@ class ClockSampler:
 
 
 def cpu_oracle_sample(w, n_loc: int, seed: int = 0, method: str = "alc"):
-    """Times the CPU oracle (as it stands) on a seeded sample of the workload's locations."""
+    """Times the CPU oracle (as it stands) on a seeded sample of the workload's locations.
+    Returns (locations per second, cores, seconds, the sample's location indices, the
+    oracle's outputs for them)."""
     import oracle
     oracle.build()
     locs = np.sort(np.random.default_rng(seed).choice(w.T, size=n_loc, replace=False))
@@ -244,7 +247,22 @@ def cpu_oracle_sample(w, n_loc: int, seed: int = 0, method: str = "alc"):
     r = oracle.predict(w.X, w.Z, w.XX[locs], w.n0, w.n, w.ncand, w.d, w.g, method, nthreads=cores)
     dt = time.perf_counter() - t0
     assert (r["status"] == 0).all()
-    return n_loc / dt, cores, dt
+    return n_loc / dt, cores, dt, locs, r
+
+
+def accuracy_vs_oracle(w, locs, ora, r, method, prec):
+    """The parity protocol of the tests (oracle/parity.py) on the oracle's sample: errors of
+    mean, s2 and var against the FP64 oracle along the GPU's path, selection match rate,
+    forced paths and near-tie steps, values admitted by each adjudication clause; for the
+    mixed screens, the FP64 re-score passes of the last timed call (all locations)."""
+    from oracle.parity import check_sample
+    gpu = {"idx": r["idx_np"], "mean": r["mean"], "s2": r["s2"], "var": r["var"]}
+    out = check_sample(w, list(locs), ora, gpu, method)
+    out["sample"] = "%d seeded locations of the %d" % (len(locs), w.T)
+    if prec == "mixed" and method != "nn":
+        out["fp64_rescore_passes"] = r["rescores"]
+        out["fp64_rescore_fraction_of_steps"] = r["rescores"] / float(w.T * (w.n - w.n0))
+    return out
 
 
 def run_reference(args):
@@ -259,7 +277,7 @@ def run_reference(args):
     times = []
     cores = os.cpu_count() or 1
     for k in range(args.steps):
-        _, cores, dt = cpu_oracle_sample(w, sample, seed=k)
+        _, cores, dt, _, _ = cpu_oracle_sample(w, sample, seed=k)
         times.append(dt)
     value = sample * len(times) / sum(times)
     line = {
@@ -345,9 +363,11 @@ def time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method="
     knn_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sel_ms = [e[1].elapsed_time(e[2]) for e in evs]
     step_ms = [a + b for a, b in zip(knn_ms, sel_ms)]
+    rescores = lagp.lagp_select_rescore_count(ws_sel, method, prec, stream)
     return dict(ms=sum(step_ms) / len(step_ms), knn_ms=sum(knn_ms) / len(knn_ms),
                 sel_ms=sum(sel_ms) / len(sel_ms), launches=int(launches), idx=idx,
-                mean=mean.cpu().numpy(), s2=s2.cpu().numpy())
+                idx_np=idx.cpu().numpy(), mean=mean.cpu().numpy(), s2=s2.cpu().numpy(),
+                var=var.cpu().numpy(), rescores=rescores)
 
 
 def max_over_ranks(values, device=None):
@@ -369,47 +389,48 @@ def barrier(torch):
         torch.cuda.synchronize()
 
 
+FP32_FMA_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+
+
 def roofline_for(prec, w, sel_ms, traffic, method="alc"):
+    """Roofline of kernels (b)+(c) for one launch over all T locations.  "frac" is always
+    the method's algorithmic work (FP64-equivalent flops of the O(j)-per-candidate design:
+    FMA = 2, exp = 20) per second of the launch against the peak of the pipe that does
+    it: FP64 DFMA for the FP64 kernels, FP32 FMA for the mixed screens (which carry that
+    work in float-float on the FP32 pipes).  For the mixed screens "issued" gives the
+    second figure: the FP32 operations the float-float arithmetic actually issues, against
+    the FP32 lane peak (one operation per lane-cycle)."""
     T, M = w.T, w.ncand
     if method == "nn":
         return None  # no scoring: kernels (b)+(c) only evaluate the predictive equations
-    if method == "mspe" and prec == "mixed":
-        work = mspe_mixed_fp32_ops_per_location(w.n0, w.n, M, w.p)
-        achieved = work * T / (sel_ms / 1e3) / 1e12
-        return {"kernel": "select_mspe_mixed_kernel (kernels b+c)", "bound": "alu",
-                "achieved": achieved, "peak": FP32_PEAK_TOPS_DERIVED, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TOPS_DERIVED, "traffic": traffic,
-                "peak_source": "derived FP32: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane-cycle)",
-                "work_per_location": work,
-                "work_unit": "FP32 operations of the float-float screen (add, mul or FMA = 1)",
-                "factor_stream_tbs": 2 * factor_stream_bytes_per_location(w.n, M) * T / (sel_ms / 1e3) / 1e12,
-                "factor_stream_note": "bytes of the two factor-row arrays read per second, kernels (b)+(c) time"}
-    if method == "mspe":
-        work = mspe_flops_per_location(w.n0, w.n, M, w.p)
-        achieved = work * T / (sel_ms / 1e3) / 1e12
-        return {"kernel": "select_mspe_kernel (kernels b+c)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "traffic": traffic,
-                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "work_per_location": work, "work_unit": "FP64 flops (FMA = 2, exp = 20)"}
+    alg = (mspe_flops_per_location if method == "mspe" else select_flops_per_location)(
+        w.n0, w.n, M, w.p)
+    achieved = alg * T / (sel_ms / 1e3) / 1e12
+    name = {("alc", "fp64"): "select_fp64_kernel", ("alc", "mixed"): "select_mixed_kernel",
+            ("mspe", "fp64"): "select_mspe_kernel",
+            ("mspe", "mixed"): "select_mspe_mixed_kernel"}[(method, prec)]
+    out = {"kernel": name + " (kernels b+c)", "bound": "alu", "achieved": achieved,
+           "unit": "TFLOP/s", "traffic": traffic, "work_per_location": alg,
+           "work_unit": "FP64-equivalent flops of the O(j)-per-candidate design (FMA = 2, exp = 20)"}
     if prec == "fp64":
-        work = select_flops_per_location(w.n0, w.n, M, w.p)
-        achieved = work * T / (sel_ms / 1e3) / 1e12
-        return {"kernel": "select_fp64_kernel (kernels b+c)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "traffic": traffic,
-                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "work_per_location": work, "work_unit": "FP64 flops (FMA = 2, exp = 20)"}
-    work = mixed_fp32_ops_per_location(w.n0, w.n, M, w.p)
-    achieved = work * T / (sel_ms / 1e3) / 1e12
-    return {"kernel": "select_mixed_kernel (kernels b+c)", "bound": "alu", "achieved": achieved,
-            "peak": FP32_PEAK_TOPS_DERIVED, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TOPS_DERIVED,
-            "traffic": traffic,
-            "peak_source": "derived FP32: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane-cycle)",
-            "work_per_location": work,
-            "work_unit": "FP32 operations of the float-float screen (add, mul or FMA = 1)",
-            "factor_stream_tbs": factor_stream_bytes_per_location(w.n, M) * T / (sel_ms / 1e3) / 1e12,
-            "factor_stream_note": "factor-row bytes read per second (shared memory + L2), kernels (b)+(c) time"}
+        out.update(peak=FP64_PEAK_TFLOPS_DERIVED, frac=achieved / FP64_PEAK_TFLOPS_DERIVED,
+                   peak_source="derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz")
+        return out
+    out.update(peak=FP32_FMA_PEAK_TFLOPS_DERIVED, frac=achieved / FP32_FMA_PEAK_TFLOPS_DERIVED,
+               peak_source="derived FP32: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz; the work "
+                           "runs in float-float on these pipes")
+    ops = (mspe_mixed_fp32_ops_per_location if method == "mspe" else mixed_fp32_ops_per_location)(
+        w.n0, w.n, M, w.p)
+    issued = ops * T / (sel_ms / 1e3) / 1e12
+    streams = 2 if method == "mspe" else 1
+    out["issued"] = {"achieved": issued, "peak": FP32_PEAK_TOPS_DERIVED, "unit": "T op/s",
+                     "frac": issued / FP32_PEAK_TOPS_DERIVED, "work_per_location": ops,
+                     "work_unit": "FP32 operations the float-float screen issues (add, mul or FMA = 1)",
+                     "peak_source": "derived FP32: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane-cycle)",
+                     "fp32_ops_per_algorithmic_flop": ops / alg}
+    out["factor_stream_tbs"] = streams * factor_stream_bytes_per_location(w.n, M) * T / (sel_ms / 1e3) / 1e12
+    out["factor_stream_note"] = "factor-row bytes read per second (shared memory + L2 + DRAM), kernels (b)+(c) time"
+    return out
 
 
 def stored_traffic(prec):
@@ -547,6 +568,90 @@ def print_stagewise(args, w, spec, variants, clocks, world):
     return 0
 
 
+def _with(args, **kw):
+    a = argparse.Namespace(**vars(args))
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def measure_single(args, wname, steps, warmup, e2e, cpu_n, acc_n_other, world=1, rank=0,
+                   locations=0):
+    """One single-design workload, every (method, precision) variant of it: kernel (a) +
+    kernels (b)+(c) timed per step with CUDA events on the launching stream (L2 flushed
+    between steps), the host entry point lagp_predict timed end to end, clocks sampled
+    during the timed region.  Then (rank 0) the CPU oracle is timed on a seeded sample
+    (cpu_n locations, all host cores: the cpu_baseline) and every variant's outputs are
+    checked against the oracle's on that sample (variants of another method: an untimed
+    sample of acc_n_other locations).  Returns the line's pieces."""
+    import torch
+    from paper_1303_0383_gb300 import lagp
+    spec = _workloads()[wname]
+    w = spec["make"]()
+    if locations:
+        w.XX = np.ascontiguousarray(w.XX[:locations])
+        if w.ZZ is not None:
+            w.ZZ = w.ZZ[:locations]
+        w.name += " (first %d locations)" % locations
+    variants_run = [v for v in spec["variants"] if args.precision == "both" or v[1] == args.precision]
+    head = spec["head"] if spec["head"] in variants_run else variants_run[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    X, Z, XX = (torch.as_tensor(a).to(dev) for a in (w.X, w.Z, w.XX))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    a2 = _with(args, steps=steps, warmup=warmup)
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit()
+                           else torch.cuda.current_device())
+    sampler.start()
+    res = {}
+    for method, prec in variants_run:
+        k = vkey(method, prec)
+        res[k] = time_precision(a2, w, prec, X, Z, XX, flush, stream, lagp, torch, method=method)
+        # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
+        res[k]["e2e_ms"] = e2e_timing(a2, w, w.ncand, method, prec, flush, res[k]["idx"]) \
+            if e2e else float("nan")
+    clocks = sampler.stop()
+    del flush
+    if world > 1:
+        for r in res.values():
+            r["ms"], r["e2e_ms"], r["sel_ms"] = max_over_ranks([r["ms"], r["e2e_ms"], r["sel_ms"]], dev)
+    if rank != 0:
+        return None
+    variants = {}
+    for method, prec in variants_run:
+        k = vkey(method, prec)
+        r = res[k]
+        variants[k] = {
+            "method": method, "precision": prec,
+            "value": world * w.T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
+            "kernels_ms": {"knn": r["knn_ms"], "select": r["sel_ms"]},
+            "e2e": {"value": world * w.T / (r["e2e_ms"] / 1e3) if r["e2e_ms"] == r["e2e_ms"] else None,
+                    "ms_per_step": r["e2e_ms"]},
+            "gpu_launches": r["launches"],
+            "roofline": roofline_for(prec, w, r["sel_ms"],
+                                     stored_traffic(prec) if (method == "alc" and wname == "paper-2d"
+                                                              and not locations) else None,
+                                     method=method),
+            "accuracy": accuracy(w, r["mean"], r["s2"]),
+        }
+    cpu = {"value": None, "cores": None, "seconds": 0.0, "n": 0}
+    if cpu_n:
+        n_cpu = min(cpu_n, w.T)
+        val, cores, dt, locs, ora = cpu_oracle_sample(w, n_cpu, method=head[0])
+        cpu = {"value": val, "cores": cores, "seconds": dt, "n": n_cpu}
+        samples = {head[0]: (locs, ora)}
+        for method, prec in variants_run:
+            if method not in samples:
+                n_o = min(acc_n_other, w.T)
+                _, _, _, l2, o2 = cpu_oracle_sample(w, n_o, seed=1, method=method)
+                samples[method] = (l2, o2)
+            locs_m, ora_m = samples[method]
+            variants[vkey(method, prec)]["accuracy_vs_oracle"] = accuracy_vs_oracle(
+                w, locs_m, ora_m, res[vkey(method, prec)], method, prec)
+    return dict(w=w, spec=spec, head=head, res=res, variants=variants, clocks=clocks, cpu=cpu)
+
+
 def run_gpu(args):
     import torch
     rank, world, local = env_rank()
@@ -554,91 +659,25 @@ def run_gpu(args):
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = torch.device("cuda", torch.cuda.current_device())
     from paper_1303_0383_gb300 import lagp
     lagp.load()
+    if args.stages:
+        return run_stagewise(args, world, rank)
     spec = _workloads()[args.workload]
-    w = spec["make"]()
-    if args.locations:
-        w.XX = np.ascontiguousarray(w.XX[: args.locations])
-        if w.ZZ is not None:
-            w.ZZ = w.ZZ[: args.locations]
-        w.name += " (first %d locations)" % args.locations
-    variants_run = [v for v in spec["variants"]
-                    if args.precision == "both" or v[1] == args.precision]
-    head = spec["head"] if spec["head"] in variants_run else variants_run[0]
-    stream = torch.cuda.current_stream()
-    X = torch.as_tensor(w.X).to(dev)
-    Z = torch.as_tensor(w.Z).to(dev)
-    XX = torch.as_tensor(w.XX).to(dev)
-    T = w.T
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
-
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
-    sampler.start()
-    res = {}
-    for method, prec in variants_run:
-        k = vkey(method, prec)
-        if args.stages:
-            # the stagewise scheme with local MLE: the paper's alc/mspe (1 stage) and
-            # alc2/mspe2 (2 stages) rows; device buffers only (no host API for it)
-            k = vkey(method + (str(args.stages) if args.stages > 1 else "") + "_mle", prec)
-            r = time_stagewise(args, w, method, prec, args.stages, X, Z, XX, flush, stream, lagp,
-                               torch)
-            r.update(knn_ms=r["kernels_ms"]["knn"], sel_ms=r["ms"] - r["kernels_ms"]["knn"],
-                     e2e_ms=float("nan"))
-            res[k] = r
-            continue
-        res[k] = time_precision(args, w, prec, X, Z, XX, flush, stream, lagp, torch, method=method)
-        # e2e: the host C ABI (lagp_predict) with pinned host buffers, copies inside the region
-        res[k]["e2e_ms"] = float("nan") if args.no_e2e else \
-            e2e_timing(args, w, w.ncand, method, prec, flush, res[k]["idx"])
-    clocks = sampler.stop()
-
-    for k, r in res.items():
-        if world > 1:
-            r["ms"], r["e2e_ms"], r["sel_ms"] = max_over_ranks([r["ms"], r["e2e_ms"], r["sel_ms"]],
-                                                               dev)
+    m = measure_single(args, args.workload, args.steps, args.warmup, not args.no_e2e,
+                       0 if args.no_cpu else (args.cpu_sample or spec["cpu"]),
+                       spec.get("acc_other", 64), world, rank, args.locations)
     if rank != 0:
         if world > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+            torch.distributed.destroy_process_group()
         return 0
-
+    w, head, res, variants = m["w"], m["head"], m["res"], m["variants"]
+    T = w.T
     h2d = T * w.p * 8
     d2h = T * (8 * 3 + 4 * w.n + 1)
-    variants = {}
-    for k, r in res.items():
-        if args.stages:
-            variants[k] = {"value": world * T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
-                           "kernels_ms": r["kernels_ms"], "gpu_launches": r["launches"],
-                           "newton_iters_mean": r["newton_iters"],
-                           "accuracy": accuracy(w, r["mean"], r["s2"])}
-            continue
-    for method, prec in ([] if args.stages else variants_run):
-        k = vkey(method, prec)
-        r = res[k]
-        variants[k] = {
-            "method": method, "precision": prec,
-            "value": world * T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
-            "kernels_ms": {"knn": r["knn_ms"], "select": r["sel_ms"]},
-            "e2e": {"value": world * T / (r["e2e_ms"] / 1e3) if r["e2e_ms"] == r["e2e_ms"] else None,
-                    "ms_per_step": r["e2e_ms"]},
-            "gpu_launches": r["launches"],
-            "roofline": roofline_for(prec, w, r["sel_ms"],
-                                     stored_traffic(prec) if (method == "alc" and args.workload == "paper-2d"
-                                                              and not args.locations) else None,
-                                     method=method),
-            "accuracy": accuracy(w, r["mean"], r["s2"]),
-        }
-    if args.stages:
-        return print_stagewise(args, w, spec, variants, clocks, world)
     hk = vkey(*head)
     H = res[hk]
-    cpu_val, cores, cpu_dt = (None, None, 0.0) if args.no_cpu else \
-        cpu_oracle_sample(w, min(args.cpu_sample or spec["cpu"], T), method=head[0])
-    paper = spec["paper"]
+    paper = m["spec"]["paper"]
     line = {
         "metric": METRIC, "value": variants[hk]["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
@@ -650,39 +689,106 @@ def run_gpu(args):
                    "ncand": w.ncand, "d": w.d, "g": w.g, "method": head[0], "precision": head[1],
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas only: each GPU runs the whole workload"},
-        "clocks": clocks,
+        "clocks": m["clocks"],
         "e2e": {"value": variants[hk]["e2e"]["value"], "unit": UNIT,
                 "ms_per_step": H["e2e_ms"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "lagp_predict (host buffers, pinned)"},
         "gpu_launches": H["launches"],
         "kernels_ms": variants[hk]["kernels_ms"],
         "roofline": variants[hk]["roofline"],
+        "accuracy_vs_oracle": variants[hk].get("accuracy_vs_oracle"),
         "variants": variants,
         "paper_form_effective_tflops": {
             k: paper_form_flops_per_location(w.n0, w.n, w.ncand) * T / (res[k]["sel_ms"] / 1e3) / 1e12
             for k in res if not k.startswith("nn")},
-        "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": m["cpu"]["value"], "unit": UNIT, "cores": m["cpu"]["cores"],
+                         "kind": "oracle",
                          "sample": "%d seeded locations of the %d, %s (%.1f s wall)" %
-                                   (min(args.cpu_sample or spec["cpu"], T), w.T, head[0], cpu_dt)},
+                                   (m["cpu"]["n"], w.T, head[0], m["cpu"]["seconds"])},
     }
     if paper:
         line["paper_context"] = {"value": paper["value"], "unit": UNIT, "what": paper["what"]}
+    # The other workloads, each timed under its own clock record: only on the default
+    # invocation at one GPU (they are measurements of their own, not part of the step).
+    if world == 1 and args.extras and args.workload == "paper-2d" and not args.locations:
+        xs, xw = min(args.steps, 5), 3
+        for name in [x for x in args.extras.split(",") if x]:
+            t0 = time.perf_counter()
+            if name == "smooth-8d":
+                line["smooth_8d"] = extra_single(args, "smooth-8d", xs, xw)
+            elif name == "batched":
+                line["batched"] = {prec: measure_batched(args, prec, xs, xw, args.batch_T)
+                                   for prec in ("mixed", "fp64")}
+            elif name == "serving":
+                line["serving"] = measure_serving([float(r) for r in args.extra_serve_rates.split(",")],
+                                                  args.extra_serve_seconds, ["mixed", "fp64"])
+            line.setdefault("extras_wall_s", {})[name] = time.perf_counter() - t0
     print(json.dumps(line), flush=True)
     if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        torch.distributed.destroy_process_group()
     return 0
 
 
-def run_batched(args):
+def extra_single(args, wname, steps, warmup):
+    """A single-design workload as an extra key of the default line: every variant's rate,
+    its roofline, its error against the oracle, its clocks (no end-to-end timing)."""
+    spec = _workloads()[wname]
+    m = measure_single(_with(args, precision="both"), wname, steps, warmup, False, spec["cpu"],
+                       spec.get("acc_other", 64))
+    w = m["w"]
+    return {"workload": w.name, "N": w.N, "p": w.p, "T": w.T, "n0": w.n0, "n": w.n, "ncand": w.ncand,
+            "d": w.d, "g": w.g, "steps": steps, "warmup": warmup, "unit": UNIT,
+            "l2": "flushed between timed steps (256 MB write)", "clocks": m["clocks"],
+            "variants": m["variants"],
+            "cpu_baseline": {"value": m["cpu"]["value"], "unit": UNIT, "cores": m["cpu"]["cores"],
+                             "kind": "oracle", "sample": "%d seeded locations, alc (%.1f s wall)"
+                             % (m["cpu"]["n"], m["cpu"]["seconds"])}}
+
+
+def run_stagewise(args, world, rank):
+    import torch
+    from paper_1303_0383_gb300 import lagp
+    spec = _workloads()[args.workload]
+    w = spec["make"]()
+    if args.locations:
+        w.XX = np.ascontiguousarray(w.XX[: args.locations])
+        if w.ZZ is not None:
+            w.ZZ = w.ZZ[: args.locations]
+        w.name += " (first %d locations)" % args.locations
+    variants_run = [v for v in spec["variants"] if args.precision == "both" or v[1] == args.precision]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    X, Z, XX = (torch.as_tensor(a).to(dev) for a in (w.X, w.Z, w.XX))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    res = {}
+    for method, prec in variants_run:
+        # the stagewise scheme with local MLE: the paper's alc/mspe (1 stage) and alc2/mspe2
+        # (2 stages) rows; device buffers only (no host API for it)
+        k = vkey(method + (str(args.stages) if args.stages > 1 else "") + "_mle", prec)
+        res[k] = time_stagewise(args, w, method, prec, args.stages, X, Z, XX, flush, stream, lagp, torch)
+    clocks = sampler.stop()
+    for r in res.values():
+        if world > 1:
+            r["ms"] = max_over_ranks([r["ms"]], dev)[0]
+    if rank != 0:
+        return 0
+    variants = {k: {"value": world * w.T / (r["ms"] / 1e3), "ms_per_step": r["ms"],
+                    "kernels_ms": r["kernels_ms"], "gpu_launches": r["launches"],
+                    "newton_iters_mean": r["newton_iters"], "accuracy": accuracy(w, r["mean"], r["s2"])}
+                for k, r in res.items()}
+    return print_stagewise(args, w, spec, variants, clocks, world)
+
+
+def measure_batched(args, prec, steps, warmup, batch_T):
     """Workload 4: uneven local problems over three resident designs in one persistent
     launch, CUDA-graph replay, launch shape tuned on the first batch."""
     import torch
     from paper_1303_0383_gb300 import inputs, lagp
     lagp.load()
-    B = inputs.batched_uneven(args.batch_T)
+    B = inputs.batched_uneven(batch_T)
     dev = torch.device("cuda", torch.cuda.current_device())
-    prec = "mixed" if args.precision in ("both", "mixed") else "fp64"
     designs = [dict(X=torch.as_tensor(w.X, device=dev), Z=torch.as_tensor(w.Z, device=dev),
                     n0=w.n0, theta=w.d, g=w.g) for w in B.designs]
     T = B.T
@@ -705,41 +811,49 @@ def run_batched(args):
     step()                       # tunes the launch shape for this signature
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()                   # captures the graph, then replays
     torch.cuda.synchronize()
     assert int((status != 0).sum()) == 0
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    sampler = ClockSampler(0)
+           for _ in range(steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     launches0 = lagp.lagp_launch_count()
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.add_(1.0)
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    print(json.dumps({
-        "metric": "local-GP predictions/sec, batched uneven problems", "value": T / (ms / 1e3),
-        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "dtype": "f32x2+f64" if prec == "mixed" else "f64",
-        "data": "synthetic", "config": {"workload": B.name, "precision": prec, "method": "alc",
-                                        "flags": "tune+graph", "first_call_s": tune_s},
-        "clocks": clocks,
-        # the library's kernels per step (graph replays count the kernels they hold)
-        "gpu_launches": (lagp.lagp_launch_count() - launches0) / args.steps}), flush=True)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    return {"metric": "local-GP predictions/sec, batched uneven problems", "value": T / (ms / 1e3),
+            "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "dtype": "f32x2+f64" if prec == "mixed" else "f64",
+            "config": {"workload": B.name, "precision": prec, "method": "alc",
+                       "flags": "tune+graph", "first_call_s": tune_s,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "clocks": clocks,
+            # the library's kernels per step (graph replays count the kernels they hold)
+            "gpu_launches": (lagp.lagp_launch_count() - launches0) / steps}
+
+
+def run_batched(args):
+    precs = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    out = {p: measure_batched(args, p, args.steps, args.warmup, args.batch_T) for p in precs}
+    line = dict(out[precs[0]])
+    line.update(n_gpus=1, higher_is_better=True, data="synthetic", variants=out)
+    print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args):
+def measure_serving(rates, seconds, precs):
     """Workload 5: Poisson arrivals of requests (1..4096 locations, log-uniform) against
     the three resident designs with n in {50, 100}; p50/p99 latency and throughput per
-    arrival rate, for the server in each precision."""
-    import threading
+    arrival rate, for the server in each precision, with the clocks of each precision's
+    run."""
     import torch
     from paper_1303_0383_gb300 import inputs, lagp
     lagp.load()
@@ -749,8 +863,6 @@ def run_serving(args):
                   n0=w.n0, theta=w.d, g=w.g) for w in B.designs]
     ncand = [1000, 2000, 2000]
     lo, hi = [-2.0, 0.0, 0.0], [2.0, 1.0, 1.0]
-    rates = [float(r) for r in args.serve_rates.split(",")]
-    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     results = {}
     for prec in precs:
         srv = lagp.Server(descs, "alc", prec, nmax=100, ncand_max=2000, max_batch=16384,
@@ -762,14 +874,15 @@ def run_serving(args):
                                  n, ncand[d])
                 srv.wait(rid, -1)
                 srv.results(rid)
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
         per_rate = {}
         for lam in rates:
             rng = np.random.default_rng(int(lam))
             sent = []
-            t_end = args.serve_seconds
             start = time.perf_counter()
             t_next = 0.0
-            while t_next < t_end:
+            while t_next < seconds:
                 L = int(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))))
                 d = int(rng.integers(0, 3))
                 n = int(rng.choice([50, 100]))
@@ -793,20 +906,26 @@ def run_serving(args):
                 "throughput_locations_per_s": locs / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean())}
+        clocks = sampler.stop()
         st = srv.stats()
         srv.close()
         results[prec] = {"rates": per_rate, "slots": st["slots"], "max_inflight": st["max_inflight"],
-                         "batches": st["batches"]}
+                         "batches": st["batches"], "clocks": clocks}
     top = str(int(max(rates)))
     head = "mixed" if "mixed" in results else precs[0]
-    print(json.dumps({
-        "metric": "serving p99 ms (Poisson arrivals, 1..4096 locations per request)",
-        "value": results[head]["rates"][top]["p99_ms"], "unit": "ms", "n_gpus": 1,
-        "higher_is_better": False, "data": "synthetic",
-        "config": {"workload": "serving over the 2-d/4-d/8-d designs, n in {50,100}, candidates "
-                               "1000/2000/2000, %g s per rate" % args.serve_seconds,
-                   "rates_locations_per_s": rates, "headline_rate": top, "precision": head},
-        "results": results}), flush=True)
+    return {"metric": "serving p99 ms (Poisson arrivals, 1..4096 locations per request)",
+            "value": results[head]["rates"][top]["p99_ms"], "unit": "ms", "higher_is_better": False,
+            "config": {"workload": "serving over the 2-d/4-d/8-d designs, n in {50,100}, candidates "
+                                   "1000/2000/2000, %g s of arrivals per rate" % seconds,
+                       "rates_locations_per_s": rates, "headline_rate": top, "precision": head},
+            "results": results}
+
+
+def run_serving(args):
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    line = measure_serving([float(r) for r in args.serve_rates.split(",")], args.serve_seconds, precs)
+    line.update(n_gpus=1, data="synthetic")
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -827,8 +946,14 @@ def main():
     ap.add_argument("--workload", default="paper-2d",
                     choices=["paper-2d", "smooth-8d", "grid-2d", "borehole", "borehole-8000", "batched",
                              "serving"])
+    ap.add_argument("--extras", default="smooth-8d,batched,serving",
+                    help="other workloads measured after the default paper-2d line and added to it "
+                         "as keys (comma list; empty: none)")
+    ap.add_argument("--no-extras", dest="extras", action="store_const", const="")
+    ap.add_argument("--extra-serve-rates", default="1000,20000,50000")
+    ap.add_argument("--extra-serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--batch-T", type=int, default=20000)
     ap.add_argument("--stages", type=int, default=0,
                     help="time the stagewise scheme with local MLE (Sec. 4.2): 1 or 2 stages")

@@ -134,6 +134,17 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
                     double *s2, double *var, int32_t *idx, int8_t *status, void *workspace,
                     size_t workspace_bytes, void *stream);
 
+/* Diagnostics of the mixed-precision screens (Sec. 3.3 decisions; no counterpart in the
+ * paper): the number of FP64 re-score passes -- steps of some location at which the screen's
+ * best scores were near-tied (or, for MSPE, G or J was a cancellation beyond the screen's
+ * resolution), so the decision was re-scored in FP64 -- made by the last lagp_select_dev,
+ * lagp_select_theta_dev, lagp_select_augment_dev or lagp_select_adaptive_dev call that ran
+ * on `workspace` with this method and precision.  Waits for the work on `stream`, then reads
+ * the count (a 4-byte device-to-host copy).  *count = 0 for LAGP_FP64 and for NN.
+ * workspace: that call's workspace (device, 256-byte aligned, at least 512 bytes). */
+int lagp_select_rescore_count(const void *workspace, size_t workspace_bytes, int32_t method,
+                              int32_t precision, int64_t *count, void *stream);
+
 /* Scratch bytes lagp_predict_dev needs (candidate lists plus both kernels' scratch). */
 size_t lagp_predict_workspace_bytes(int64_t N, int64_t T, int32_t p, int32_t n,
                                     int32_t ncand, int32_t method, int32_t precision);
@@ -233,7 +244,9 @@ int lagp_server_destroy(lagp_server *s);
  * cudaMalloc, no cudaFree, no allocating library routine); inputs and outputs are the
  * caller's device buffers, with the meaning, layout and rules of lagp_select_dev.
  *   - The first call on a device looks up the array's device address with that device
- *     current; make that first call before any stream capture.
+ *     current; make that first call before any stream capture.  The address is cached
+ *     for that CUDA context: after a cudaDeviceReset the first call in the device's new
+ *     context looks it up again (so it, too, should come before any capture).
  *   - All calls share the array, which keeps the previous call's contents; the call
  *     clears the part that must start at zero.  Calls whose kernels overlap on the GPU
  *     (for example on two streams) race on the array: serialise them.
@@ -262,8 +275,8 @@ int lagp_exp_dev(const double *x, double *y, int64_t n, void *stream);
  * region launched. */
 int64_t lagp_launch_count(void);
 
-/* Design augmentation (Sec. 6: with the indices of the local designs saved, "designs can
- * be augmented, picking up where they left off"): kernels (b)+(c) where location t's
+/* Design augmentation (Sec. 6: once the indices of the local designs are saved, a design
+ * can later be extended from where its construction stopped): kernels (b)+(c) where location t's
  * design starts from the n1 saved points start[t*n1 .. t*n1+n1) (design indices in
  * selection order, e.g. a previous call's idx) instead of its n0 nearest neighbours, and
  * grows greedily to n points.  The greedy choice depends only on the current design, so

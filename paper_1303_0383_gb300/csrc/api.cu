@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of liblagp (declared in include/lagp.h): argument checks, the
 // resident design handle, scratch sizing and the host-buffer wrapper around the device
 // path.  All arithmetic of the method runs in the kernels of knn.cu and select.cu.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -48,6 +49,36 @@ int dev_info(DevInfo *out) {
   }
   *out = cache[dev];
   return LAGP_OK;
+}
+
+// The unique id of the calling thread's current CUDA context (0 if it has none yet).  The
+// per-device caches of device addresses and constant uploads are keyed on it: after a
+// cudaDeviceReset the device's next context is a new one, whose constant banks are not
+// uploaded and whose symbol addresses may differ.  The driver functions are reached
+// through the runtime, so the library does not link the driver library itself.
+int current_context_id(unsigned long long *id) {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static std::once_flag once;
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  *id = 0;
+  if (!get_current || !get_id) return LAGP_ERR_CUDA;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS) return LAGP_ERR_CUDA;
+  if (!c) return LAGP_OK;
+  return get_id(c, id) == CUDA_SUCCESS ? LAGP_OK : LAGP_ERR_CUDA;
 }
 
 int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t ncand,
@@ -179,6 +210,26 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
   a.method = method; a.precision = precision;
   a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int lagp_select_rescore_count(const void *workspace, size_t workspace_bytes, int32_t method,
+                              int32_t precision, int64_t *count, void *stream) {
+  if (!count) return LAGP_ERR_INVALID_ARG;
+  if (method != LAGP_ALC && method != LAGP_MSPE && method != LAGP_NN) return LAGP_ERR_INVALID_ARG;
+  if (precision != LAGP_FP64 && precision != LAGP_MIXED) return LAGP_ERR_INVALID_ARG;
+  *count = 0;
+  if (precision != LAGP_MIXED || method == LAGP_NN) return LAGP_OK;
+  if (!workspace || workspace_bytes < 512 || ((uintptr_t)workspace & 255) != 0)
+    return LAGP_ERR_INVALID_ARG;
+  // the mixed screens keep the count at byte 256 of their workspace (cleared at launch)
+  int32_t v = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&v, static_cast<const char *>(workspace) + 256, sizeof(v),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  *count = v;
+  return LAGP_OK;
 }
 
 size_t lagp_predict_workspace_bytes(int64_t N, int64_t T, int32_t p, int32_t n, int32_t ncand,

@@ -37,21 +37,28 @@ struct ExpConsts {
 const ExpConsts *exp_host_consts();
 
 // Each translation unit that includes this header has its own constant-bank copy
-// (no relocatable device code is needed) and uploads it once per device.
+// (no relocatable device code is needed) and uploads it once per CUDA context: a
+// cudaDeviceReset ends the context, and the device's next one is uploaded afresh.  The
+// upload must not happen during stream capture (the *_prepare calls do it beforehand).
 static __constant__ ExpConsts c_exp;
 
 static int exp_table_upload() {
   static std::mutex mu;
-  static bool ready[64];
+  static unsigned long long ctx[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
   if (dev < 0 || dev >= 64) return LAGP_ERR_CUDA;
   std::lock_guard<std::mutex> lk(mu);
-  if (!ready[dev]) {
+  unsigned long long id = 0;
+  int st = current_context_id(&id);
+  if (st) return st;
+  if (id == 0 || ctx[dev] != id) {
     e = cudaMemcpyToSymbol(c_exp, exp_host_consts(), sizeof(ExpConsts));
     if (e != cudaSuccess) return cuda_status(e);
-    ready[dev] = true;
+    st = current_context_id(&id);  // the copy made the context current if there was none
+    if (st) return st;
+    ctx[dev] = id;
   }
   return LAGP_OK;
 }

@@ -157,6 +157,9 @@ int check_common(int64_t N, int32_t p, int64_t T, int32_t n0, int32_t n, int32_t
                  double theta, double g, int32_t method, int32_t precision);
 int check_supported(int32_t method, int32_t precision);
 
+// Unique id of the calling thread's current CUDA context, 0 if none (api.cu).
+int current_context_id(unsigned long long *id);
+
 // Map the last CUDA error to a library code.
 int cuda_status(cudaError_t e);
 

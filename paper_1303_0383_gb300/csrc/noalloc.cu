@@ -3,8 +3,9 @@
 //
 // The array below is defined once per process and exists on every device that loads
 // the library until the process exits.  Host code cannot use its name as a device
-// address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current, checks the result, and caches it.
+// address, so the first call in each CUDA context looks the address up with
+// cudaGetSymbolAddress while that device is current, checks the result, and caches it
+// for that context (after a cudaDeviceReset the device's next context looks it up again).
 // Every call reuses the same bytes: the launcher clears the work counter it needs at
 // zero, and two calls whose kernels overlap on the GPU would corrupt each other.
 #include <mutex>
@@ -18,21 +19,26 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[LAGP_NOALLOC_SC
 
 std::mutex g_scratch_mu;
 void *g_scratch_ptr[64];
-bool g_scratch_ready[64];
+unsigned long long g_scratch_ctx[64];  // the context the cached address belongs to
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+// Device address of g_noalloc_scratch on the current device (looked up once per context).
 int noalloc_scratch(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
   if (dev < 0 || dev >= 64) return LAGP_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ready[dev]) {
+  unsigned long long id = 0;
+  int st = current_context_id(&id);
+  if (st) return st;
+  if (id == 0 || g_scratch_ctx[dev] != id) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) return cuda_status(e != cudaSuccess ? e : cudaErrorUnknown);
+    st = current_context_id(&id);  // the lookup made the context current if there was none
+    if (st) return st;
     g_scratch_ptr[dev] = p;
-    g_scratch_ready[dev] = true;
+    g_scratch_ctx[dev] = id;
   }
   *out = g_scratch_ptr[dev];
   return LAGP_OK;

@@ -64,6 +64,7 @@ def load(path: str | None = None):
     L.lagp_select_workspace_bytes.restype = sz
     L.lagp_select_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64, i32, i32,
                                   P, P, P, P, P, P, sz, P]
+    L.lagp_select_rescore_count.argtypes = [P, sz, i32, i32, ctypes.POINTER(i64), P]
     L.lagp_predict_workspace_bytes.argtypes = [i64, i64, i32, i32, i32, i32, i32]
     L.lagp_predict_workspace_bytes.restype = sz
     L.lagp_predict_dev.argtypes = [P, P, i64, i32, P, i64, i32, i32, i32, f64, f64, i32, i32,
@@ -177,6 +178,16 @@ def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2
                                 _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
                                 _dp(status), _dp(ws), ws.numel(), _stream(stream)),
          "lagp_select_dev")
+
+
+def lagp_select_rescore_count(ws, method="alc", precision="mixed", stream=None) -> int:
+    """FP64 re-score passes made by the last selection call on workspace ws (mixed screens;
+    0 for FP64 and NN)."""
+    out = ctypes.c_int64()
+    _chk(load().lagp_select_rescore_count(_dp(ws), ws.numel() * ws.element_size(), _m(method),
+                                          _pr(precision), ctypes.byref(out), _stream(stream)),
+         "lagp_select_rescore_count")
+    return int(out.value)
 
 
 def lagp_exp_dev(x, y, stream=None) -> None:

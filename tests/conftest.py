@@ -25,3 +25,19 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Every value that passed the parity protocol only by an adjudication clause (past
+    1e-10 against the FP64 oracle), counted per clause with the largest error admitted."""
+    if "oracle.parity" not in sys.modules:
+        return
+    from oracle.parity import CLAUSES, tally_summary
+    tr = terminalreporter
+    s = tally_summary()
+    tr.write_sep("-", "parity adjudication (values past 1e-10 against the FP64 oracle)")
+    if not s:
+        tr.write_line("none: every compared value within 1e-10 of the FP64 oracle")
+    for c, d in s.items():
+        tr.write_line("clause %d (%s): %d values, largest relative error %.3g"
+                      % (c, CLAUSES[c], d["values"], d["max_rel_err"]))
