@@ -62,6 +62,7 @@ extern "C" {
 #define LAGP_ERR_UNSUPPORTED (-7)
 #define LAGP_ERR_SCRATCH_LIMIT (-8)
 #define LAGP_ERR_NO_CONVERGENCE (-9)
+#define LAGP_ERR_CANCELLED (-10)
 
 typedef enum { LAGP_ALC = 0, LAGP_MSPE = 1, LAGP_NN = 2 } lagp_method;
 
@@ -215,7 +216,8 @@ int lagp_predict_batch_dev(const lagp_design_desc *designs, int32_t ndesigns, co
  * fits the budget).  submit copies XX (host, L x p) and returns at once; wait blocks up
  * to timeout_ms (negative: no limit) for a request; results copies a finished request's
  * outputs to host buffers (mean, s2, var: L; idx: L x n; status: L; any may be NULL),
- * gives its latency from submit to completion in ms, and forgets the request. */
+ * gives its latency from submit to completion in ms, and forgets the request; for a request
+ * whose batch failed (or that was cancelled) it returns that code instead and forgets it. */
 typedef struct lagp_server lagp_server;
 int lagp_server_create(const lagp_design_desc *designs, int32_t ndesigns, int32_t method,
                        int32_t precision, int32_t nmax, int32_t ncand_max, int64_t max_batch,
@@ -230,6 +232,31 @@ int lagp_server_results(lagp_server *s, uint64_t request_id, double *mean, doubl
 int lagp_server_stats(lagp_server *s, int64_t *batches, int64_t *locations, int32_t *slots,
                       int32_t *max_inflight);
 int lagp_server_destroy(lagp_server *s);
+
+/* Device bytes of one in-flight slot of a server created with these arguments (its buffers
+ * and the workspace of the largest batch it accepts); 0 if the arguments are invalid.  A
+ * memory_budget of k times this gives min(k, max_slots) slots; below it, create returns
+ * LAGP_ERR_OOM (admission refused).  The paper has no counterpart. */
+size_t lagp_server_slot_bytes(const lagp_design_desc *designs, int32_t ndesigns, int32_t method,
+                              int32_t precision, int32_t nmax, int32_t ncand_max,
+                              int64_t max_batch);
+
+/* Cancels a request that has not completed.  A request still queued leaves the queue and
+ * never reaches the GPU; a request whose batch is already on the GPU lets that batch run to
+ * completion (the other requests in it are unaffected) and drops its own outputs.  Either
+ * way the request completes at once or with its batch, and lagp_server_results then returns
+ * LAGP_ERR_CANCELLED (and forgets it).  Returns LAGP_ERR_INVALID_ARG for an unknown or
+ * already completed request.  The paper has no counterpart. */
+int lagp_server_cancel(lagp_server *s, uint64_t request_id);
+
+/* Test hook for the server's failure path (the paper has no counterpart): marks a request
+ * that is still queued so that the batch holding it -- the scheduler gives it a batch of
+ * its own -- fails on the host with `code` (< 0) in place of the batched call's return code,
+ * before any GPU work.  The request completes with that code (lagp_server_results returns
+ * it), lagp_server_stats reports it as the last error, and every other request is served as
+ * usual.  Returns LAGP_ERR_INVALID_ARG if the request is unknown or no longer queued, or if
+ * code >= 0. */
+int lagp_server_inject_error(lagp_server *s, uint64_t request_id, int32_t code);
 
 /* ------------------------------------------------------------------ no-allocation variant */
 /* Kernels (b)+(c) as lagp_select_dev, for callers that cannot allocate device memory: a

@@ -126,6 +126,7 @@ const char *lagp_strerror(int code) {
     case LAGP_ERR_UNSUPPORTED: return "method/precision combination not supported by this build";
     case LAGP_ERR_SCRATCH_LIMIT: return "problem too large for the static scratch of the no-allocation entry point";
     case LAGP_ERR_NO_CONVERGENCE: return "iteration limit reached before the stopping rule was met";
+    case LAGP_ERR_CANCELLED: return "request cancelled";
     default: return "unknown error code";
   }
 }

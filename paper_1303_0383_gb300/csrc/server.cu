@@ -40,6 +40,8 @@ struct Request {
   Clock::time_point t_submit, t_done;
   int code = 0;
   bool done = false;
+  bool cancelled = false;  // cancelled while its batch was on the GPU: outputs dropped
+  int inject = 0;          // test hook: the batch holding it fails with this code, on the host
 };
 
 struct Slot {
@@ -102,18 +104,45 @@ Offsets dev_offsets(int64_t T, int32_t nmax) {
 
 // Workspace of the worst batch a slot accepts: max_batch locations, all with nmax and Mmax,
 // spread over every design (the largest N and p).
-size_t worst_workspace(const lagp_server *S) {
-  const int nd = (int)S->designs.size();
-  std::vector<int32_t> dof(S->max_batch), n(S->max_batch, S->nmax), m(S->max_batch);
-  for (int64_t t = 0; t < S->max_batch; t++) {
+size_t worst_workspace(const lagp_design_desc *designs, int nd, int32_t method, int32_t precision,
+                       int32_t nmax, int32_t Mmax, int64_t max_batch) {
+  std::vector<int32_t> dof(max_batch), n(max_batch, nmax), m(max_batch);
+  for (int64_t t = 0; t < max_batch; t++) {
     dof[t] = (int32_t)(t % nd);
-    m[t] = (int32_t)std::min<int64_t>(S->Mmax, S->designs[dof[t]].N);
+    m[t] = (int32_t)std::min<int64_t>(Mmax, designs[dof[t]].N);
   }
-  return lagp_predict_batch_workspace_bytes(S->designs.data(), nd, S->max_batch, dof.data(),
-                                            n.data(), m.data(), S->method, S->precision);
+  return lagp_predict_batch_workspace_bytes(designs, nd, max_batch, dof.data(), n.data(), m.data(),
+                                            method, precision);
+}
+
+// Device bytes of one in-flight slot (its buffers and the worst batch's workspace), 0 if the
+// arguments are invalid.
+size_t slot_device_bytes(const lagp_design_desc *designs, int nd, int32_t method,
+                         int32_t precision, int32_t nmax, int32_t Mmax, int64_t max_batch) {
+  const size_t ws = worst_workspace(designs, nd, method, precision, nmax, Mmax, max_batch);
+  if (ws == 0) return 0;
+  return dev_offsets(max_batch, nmax).total + ws;
+}
+
+// A batch that fails before reaching the GPU: its requests complete with the code at once.
+void fail_batch_now(lagp_server *S, std::vector<std::shared_ptr<Request>> &reqs, int code) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  const auto now = Clock::now();
+  for (auto &r : reqs) {
+    r->code = r->cancelled ? LAGP_ERR_CANCELLED : code;
+    r->done = true;
+    r->t_done = now;
+  }
+  S->last_error = code;
+  S->cv_done.notify_all();
 }
 
 void run_batch(lagp_server *S, Slot &sl, std::vector<std::shared_ptr<Request>> &&reqs) {
+  for (auto &r : reqs)
+    if (r->inject) {  // a request marked by lagp_server_inject_error runs in a batch alone
+      fail_batch_now(S, reqs, r->inject);
+      return;
+    }
   sl.reqs = std::move(reqs);
   int64_t T = 0, itot = 0;
   for (auto &r : sl.reqs) { T += r->L; itot += r->L * r->n; }
@@ -173,7 +202,17 @@ void finish_batch(lagp_server *S, Slot &sl) {
   const auto now = Clock::now();
   int64_t t = 0, io = 0;
   std::lock_guard<std::mutex> lk(S->mu);
+  int64_t served = 0;
   for (auto &r : sl.reqs) {
+    if (r->cancelled) r->code = LAGP_ERR_CANCELLED;
+    if (r->code) {
+      t += r->L;
+      io += r->L * r->n;
+      r->t_done = now;
+      r->done = true;
+      continue;
+    }
+    served += r->L;
     r->mean.assign(hm + t, hm + t + r->L);
     r->s2.assign(hs + t, hs + t + r->L);
     r->var.assign(hv + t, hv + t + r->L);
@@ -185,7 +224,7 @@ void finish_batch(lagp_server *S, Slot &sl) {
     r->done = true;
   }
   S->batches++;
-  S->locations += sl.T;
+  S->locations += served;
   sl.reqs.clear();
   sl.busy = false;
   S->cv_done.notify_all();
@@ -202,7 +241,11 @@ void scheduler(lagp_server *S) {
       if (q == cudaSuccess) finish_batch(S, sl);
       else if (q != cudaErrorNotReady) {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (auto &r : sl.reqs) { r->code = LAGP_ERR_CUDA; r->done = true; r->t_done = Clock::now(); }
+        for (auto &r : sl.reqs) {
+          r->code = r->cancelled ? LAGP_ERR_CANCELLED : LAGP_ERR_CUDA;
+          r->done = true;
+          r->t_done = Clock::now();
+        }
         sl.reqs.clear();
         sl.busy = false;
         S->last_error = LAGP_ERR_CUDA;
@@ -221,9 +264,12 @@ void scheduler(lagp_server *S) {
       if (free_slot) {
         int64_t T = 0;
         while (!S->pending.empty() && T + S->pending.front()->L <= S->max_batch) {
+          const bool alone = S->pending.front()->inject != 0;
+          if (alone && !take.empty()) break;
           T += S->pending.front()->L;
           take.push_back(S->pending.front());
           S->pending.pop_front();
+          if (alone) break;
         }
       }
       if (take.empty()) {
@@ -264,10 +310,10 @@ int lagp_server_create(const lagp_design_desc *designs, int32_t ndesigns, int32_
   S->Mmax = ncand_max;
   S->max_batch = max_batch;
   cudaGetDevice(&S->device);
-  const size_t ws = worst_workspace(S);
-  if (ws == 0) { delete S; return LAGP_ERR_INVALID_ARG; }
-  const Offsets o = dev_offsets(max_batch, nmax);
-  const size_t slot_dev = o.total + ws;
+  const size_t slot_dev = slot_device_bytes(designs, ndesigns, method, precision, nmax, ncand_max,
+                                            max_batch);
+  if (slot_dev == 0) { delete S; return LAGP_ERR_INVALID_ARG; }
+  const size_t ws = slot_dev - dev_offsets(max_batch, nmax).total;
   int nslots = (int)std::min<size_t>((size_t)max_slots, memory_budget / slot_dev);
   if (nslots < 1) { delete S; return LAGP_ERR_OOM; }
   S->slots.resize(nslots);
@@ -349,6 +395,47 @@ int lagp_server_results(lagp_server *S, uint64_t id, double *mean, double *s2, d
   if (latency_ms)
     *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   return LAGP_OK;
+}
+
+size_t lagp_server_slot_bytes(const lagp_design_desc *designs, int32_t ndesigns, int32_t method,
+                              int32_t precision, int32_t nmax, int32_t ncand_max,
+                              int64_t max_batch) {
+  if (!designs || ndesigns < 1 || nmax < 3 || nmax > kMaxN || ncand_max < nmax ||
+      ncand_max > kMaxCand || max_batch < 1)
+    return 0;
+  return slot_device_bytes(designs, ndesigns, method, precision, nmax, ncand_max, max_batch);
+}
+
+int lagp_server_cancel(lagp_server *S, uint64_t id) {
+  if (!S) return LAGP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end() || it->second->done) return LAGP_ERR_INVALID_ARG;
+  auto r = it->second;
+  for (auto q = S->pending.begin(); q != S->pending.end(); ++q)
+    if (*q == r) {  // still queued: it never reaches the GPU
+      S->pending.erase(q);
+      r->code = LAGP_ERR_CANCELLED;
+      r->done = true;
+      r->t_done = Clock::now();
+      S->cv_done.notify_all();
+      return LAGP_OK;
+    }
+  r->cancelled = true;  // in a batch on the GPU: the batch finishes, this request's outputs are dropped
+  return LAGP_OK;
+}
+
+int lagp_server_inject_error(lagp_server *S, uint64_t id, int32_t code) {
+  if (!S || code >= 0) return LAGP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end()) return LAGP_ERR_INVALID_ARG;
+  for (auto &q : S->pending)
+    if (q == it->second) {
+      q->inject = code;
+      return LAGP_OK;
+    }
+  return LAGP_ERR_INVALID_ARG;  // already in a batch or finished
 }
 
 int lagp_server_stats(lagp_server *S, int64_t *batches, int64_t *locations, int32_t *slots,

@@ -24,6 +24,7 @@ LAGP_ERR_NOT_PD = -5
 LAGP_ERR_NO_DEVICE = -6
 LAGP_ERR_UNSUPPORTED = -7
 LAGP_ERR_SCRATCH_LIMIT = -8
+LAGP_ERR_CANCELLED = -10
 
 LAGP_ALC, LAGP_MSPE, LAGP_NN = 0, 1, 2
 LAGP_FP64, LAGP_MIXED = 0, 1
@@ -77,6 +78,10 @@ def load(path: str | None = None):
     L.lagp_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                     ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.lagp_server_destroy.argtypes = [P]
+    L.lagp_server_slot_bytes.argtypes = [P, i32, i32, i32, i32, i32, i64]
+    L.lagp_server_slot_bytes.restype = sz
+    L.lagp_server_cancel.argtypes = [P, ctypes.c_uint64]
+    L.lagp_server_inject_error.argtypes = [P, ctypes.c_uint64, i32]
     L.lagp_predict_batch_workspace_bytes.argtypes = [P, i32, i64, P, P, P, i32, i32]
     L.lagp_predict_batch_workspace_bytes.restype = sz
     L.lagp_predict_batch_dev.argtypes = [P, i32, P, i32, i64, P, P, P, i32, i32, P, P, P, P, P,
@@ -238,6 +243,13 @@ def lagp_predict_batch_dev(designs, XX, design_of, n, ncand, method, precision, 
                                        ws.numel(), _stream(stream)), "lagp_predict_batch_dev")
 
 
+def lagp_server_slot_bytes(designs, method="alc", precision="mixed", nmax=128, ncand_max=2048,
+                           max_batch=16384) -> int:
+    """Device bytes of one slot of a server created with these arguments."""
+    return int(load().lagp_server_slot_bytes(_descs(designs), len(designs), _m(method), _pr(precision),
+                                             nmax, ncand_max, max_batch))
+
+
 class Server:
     """lagp_server_*: continuous-batching serving loop over resident designs."""
 
@@ -276,6 +288,22 @@ class Server:
                                         ctypes.byref(lat)), "lagp_server_results")
         out["latency_ms"] = lat.value
         return out
+
+    def cancel(self, rid) -> int:
+        """Cancels a request (lagp_server_cancel); returns the library's code."""
+        return int(load().lagp_server_cancel(self._h, rid))
+
+    def inject_error(self, rid, code) -> int:
+        """Test hook: the queued request's batch fails on the host with code."""
+        return int(load().lagp_server_inject_error(self._h, rid, code))
+
+    def try_results(self, rid):
+        """results(), but a failed or cancelled request gives (code, None) instead of raising."""
+        try:
+            return 0, self.results(rid)
+        except LagpError as e:
+            self._n.pop(rid, None)
+            return e.code, None
 
     def stats(self):
         b, l, s, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
