@@ -102,12 +102,12 @@ def mixed_fp32_ops_per_location(n0, n, M, p):
     """FP32 operations (add, multiply or fused multiply-add, each one) of the float-float
     screen for one location: every pool candidate at step j costs 12j + 6 (the compensated
     row dot: TwoProd with cross terms and TwoSum per term, one renormalisation) + 20p + 3
-    (squared distance) + 11 (scaling by 1/theta) + 66 (float-float exponential) + 9 (new
-    row entry) + 42 (v and cov updates) + 6 (screen score)."""
+    (squared distance of coordinates pre-scaled by 1/sqrt(theta)) + 66 (float-float
+    exponential) + 9 (new row entry) + 42 (v and cov updates) + 6 (screen score)."""
     total = 0
     for j in range(n - 1):
         pool = M - (j + 1)
-        total += pool * (12 * j + 6 + 20 * p + 3 + 11 + 66 + 9 + 42 + 6)
+        total += pool * (12 * j + 6 + 20 * p + 3 + 66 + 9 + 42 + 6)
     return float(total)
 
 
