@@ -36,6 +36,8 @@ namespace {
 
 constexpr int KB = 256;               // threads per CTA
 constexpr int HBITS = 12;
+constexpr int KS = 16;                // the sample that bounds the M-th distance: one block of
+                                      // 32 consecutive design points in every KS blocks
 constexpr int HBINS = 1 << HBITS;     // 4096 histogram bins
 // The bucket sort's permutation gets cap entries of its own where they fit in shared
 // memory next to the keys (cap <= 8192); otherwise it uses the histogram's second half
@@ -270,6 +272,24 @@ __device__ __forceinline__ float sqdist_f32(const float *xf, const float *__rest
   return acc;
 }
 
+// Visits the points i = first, first + stride, ... < N: the FP32 distances of KU points are
+// formed -- their loads in flight together -- before f(d2f, i) uses any of them (one point
+// at a time, each pass was bound by the L2 latency of its dependent loads).
+constexpr int KU = 4;
+template <int P, typename F>
+__device__ __forceinline__ void each_point(const float *xf, const float *__restrict__ Xf, int N,
+                                           int p, int first, int stride, F f) {
+  int i = first;
+  for (; i + (KU - 1) * stride < N; i += KU * stride) {
+    float d[KU];
+#pragma unroll
+    for (int u = 0; u < KU; u++) d[u] = sqdist_f32<P>(xf, Xf, i + u * stride, N, p);
+#pragma unroll
+    for (int u = 0; u < KU; u++) f(d[u], i + u * stride);
+  }
+  for (; i < N; i += stride) f(sqdist_f32<P>(xf, Xf, i, N, p), i);
+}
+
 constexpr int BUCKET_CAP = 32; // largest bucket sorted in place; beyond, the bitonic sort
 
 // Rank order of the cnt survivors (keys (d2 hi, d2 lo, index) in kh/kl/sidx) by a bucket
@@ -289,15 +309,29 @@ __device__ bool bucket_order(const uint32_t *kh, const uint32_t *kl, const int32
     *sh_flag = 0u;
   }
   for (int b = threadIdx.x; b < nb; b += KB) bound[b] = 0;
+  // the largest key (non-negative doubles order like their bits): a warp maximum, then one
+  // shared atomic per warp
+  unsigned long long wmax = 0ull;
+  for (int r = threadIdx.x; r < cnt; r += KB) {
+    const unsigned long long k = ((unsigned long long)kh[r] << 32) | kl[r];
+    wmax = k > wmax ? k : wmax;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, wmax, o);
+    wmax = w > wmax ? w : wmax;
+  }
   __syncthreads();
-  for (int r = threadIdx.x; r < cnt; r += KB)
-    atomicMax(sh_dmax, ((unsigned long long)kh[r] << 32) | kl[r]);  // non-negative doubles order like their bits
+  if ((threadIdx.x & 31) == 0 && wmax) atomicMax(sh_dmax, wmax);
   __syncthreads();
-  const double dmax = __longlong_as_double((long long)*sh_dmax);
-  if (!(dmax > 0.0)) return false;
-  const double scale = (double)(nb - 1) / dmax;
+  // buckets from FP32: float(d2) is non-decreasing in d2 and so is its product with a
+  // positive scale and the truncation, so bucket order is distance order (equal floats
+  // share a bucket, which the insertion below orders by the exact key)
+  const float dmax = __double2float_ru(__longlong_as_double((long long)*sh_dmax));
+  if (!(dmax > 0.0f)) return false;
+  const float scale = (float)(nb - 1) / dmax;
   auto bucket_of = [&](int r) {
-    const double d2 = __longlong_as_double((long long)(((unsigned long long)kh[r] << 32) | kl[r]));
+    const float d2 = __double2float_rn(
+        __longlong_as_double((long long)(((unsigned long long)kh[r] << 32) | kl[r])));
     const int b = (int)(d2 * scale);
     return b < nb - 1 ? b : nb - 1;
   };
@@ -347,7 +381,7 @@ __device__ bool bucket_order(const uint32_t *kh, const uint32_t *kl, const int32
 // candidate count and output offset) and the row stride of XX; uniform launches pass
 // nullptr and use M, t*M and t*p.
 template <int P>
-__global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, int N, int p,
+__global__ void __launch_bounds__(KB, 4) knn_kernel(const double *__restrict__ X, int N, int p,
                                                  const double *__restrict__ XX, int64_t T, int M,
                                                  int32_t *__restrict__ cand,
                                                  const float *__restrict__ Xf,
@@ -387,33 +421,99 @@ __global__ void __launch_bounds__(KB) knn_kernel(const double *__restrict__ X, i
     for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
     if (threadIdx.x == 0) sh_count = 0;
     __syncthreads();
-    // pass 1: histogram of the FP32 distances
-    for (int i = threadIdx.x; i < N; i += KB) {
-      const float d2f = sqdist_f32<P>(xf, Xf, i, N, p);
-      atomicAdd(&hist[__float_as_uint(d2f) >> (31 - HBITS)], 1u);
-    }
-    __syncthreads();
-    find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, &sh_bin, &sh_below);
-    if (threadIdx.x == 0) {
-      double B = Bx;
-      for (int k = 0; k < p; k++) B = fmax(B, fabs(xs[k]));
-      const double tau = (double)__uint_as_float(((uint32_t)sh_bin + 1u) << (31 - HBITS));
-      const double E0 = fp32_err_bound(tau, B, p);
-      const double E = fp32_err_bound(tau + 2.0 * E0, B, p);
-      sh_thr = __double2float_ru(tau + 2.0 * E);
-    }
-    __syncthreads();
-    const float thr = sh_thr;
-    // pass 2: the same FP32 distances again (bit for bit); survivors are listed first
-    for (int i = threadIdx.x; i < N; i += KB) {
-      const float d2f = sqdist_f32<P>(xf, Xf, i, N, p);
-      if (d2f <= thr) {
-        const uint32_t pos = atomicAdd(&sh_count, 1u);
-        if (pos < (uint32_t)cap) sidx[pos] = i;
+    // The screen's threshold thr = tau + 2E: tau the upper edge of the bin holding the M-th
+    // smallest d2f in `hist` (complete up to that bin), E the FP32 error bound.
+    auto set_threshold = [&]() {
+      find_rank_bin(hist, HBINS, (uint32_t)M, warp_tmp, &sh_bin, &sh_below);
+      if (threadIdx.x == 0) {
+        double B = Bx;
+        for (int k = 0; k < p; k++) B = fmax(B, fabs(xs[k]));
+        const double tau = (double)__uint_as_float(((uint32_t)sh_bin + 1u) << (31 - HBITS));
+        const double E0 = fp32_err_bound(tau, B, p);
+        const double E = fp32_err_bound(tau + 2.0 * E0, B, p);
+        sh_thr = __double2float_ru(tau + 2.0 * E);
+      }
+      __syncthreads();
+    };
+    int cnt = 0;
+    bool listed = false;
+    // pass 0: a sample of the design -- 32 consecutive points (one coalesced warp load per
+    // coordinate) out of every 32 KS, spread over any ordering of X -- bounds the M-th
+    // smallest d2f from above: bound = the upper edge of the bin holding the sample's
+    // ceil(1.5 M ns / N)-th smallest, about 1.5 M points of the whole design
+    const int ns = (N / (32 * KS)) * 32 + min(32, N % (32 * KS));
+    const int ks = (int)(((int64_t)3 * M * ns + 2 * (int64_t)N - 1) / (2 * (int64_t)N));
+    if (ks < ns) {
+      each_point<P>(xf, Xf, N, p, (threadIdx.x >> 5) * 32 * KS + (threadIdx.x & 31),
+                    (KB / 32) * 32 * KS, [&](float d2f, int) {
+        atomicAdd(&hist[__float_as_uint(d2f) >> (31 - HBITS)], 1u);
+      });
+      __syncthreads();
+      find_rank_bin(hist, HBINS, (uint32_t)ks, warp_tmp, &sh_bin, &sh_below);
+      const float bound = __uint_as_float(((uint32_t)sh_bin + 1u) << (31 - HBITS));
+      for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
+      __syncthreads();
+      // pass 1: the points with d2f <= bound are listed (d2f bits, index) and histogrammed;
+      // the list's histogram is the whole design's in every bin up to the M-th's
+      each_point<P>(xf, Xf, N, p, threadIdx.x, KB, [&](float d2f, int i) {
+        if (d2f <= bound) {
+          const uint32_t pos = atomicAdd(&sh_count, 1u);
+          if (pos < (uint32_t)cap) {
+            kh[pos] = __float_as_uint(d2f);
+            kl[pos] = (uint32_t)i;
+          }
+          atomicAdd(&hist[__float_as_uint(d2f) >> (31 - HBITS)], 1u);
+        }
+      });
+      __syncthreads();
+      const uint32_t nl = sh_count;
+      if (nl >= (uint32_t)M && nl <= (uint32_t)cap) {
+        set_threshold();
+        const float thr = sh_thr;
+        if (thr <= bound) {  // every point with d2f <= thr is in the list: keep those
+          listed = true;
+          __syncthreads();
+          if (threadIdx.x == 0) sh_count = 0;
+          __syncthreads();
+          // warp-aggregated appends: one shared atomic per warp and pass
+          for (int r0 = threadIdx.x & ~31; r0 < (int)nl; r0 += KB) {
+            const int r = r0 + (threadIdx.x & 31);
+            const bool keep = r < (int)nl && __uint_as_float(kh[r]) <= thr;
+            const unsigned ball = __ballot_sync(0xffffffffu, keep);
+            uint32_t base = 0;
+            if ((threadIdx.x & 31) == 0 && ball) base = atomicAdd(&sh_count, (uint32_t)__popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) sidx[base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u))] = (int32_t)kl[r];
+          }
+          __syncthreads();
+          cnt = (int)sh_count;
+        }
+      }
+      if (!listed) {  // the sample's bound missed (rare): the two full passes below
+        __syncthreads();
+        for (int b = threadIdx.x; b < HBINS; b += KB) hist[b] = 0;
+        if (threadIdx.x == 0) sh_count = 0;
+        __syncthreads();
       }
     }
-    __syncthreads();
-    int cnt = (int)sh_count;
+    if (!listed) {
+      // pass 1: histogram of the FP32 distances of every point
+      each_point<P>(xf, Xf, N, p, threadIdx.x, KB, [&](float d2f, int) {
+        atomicAdd(&hist[__float_as_uint(d2f) >> (31 - HBITS)], 1u);
+      });
+      __syncthreads();
+      set_threshold();
+      const float thr = sh_thr;
+      // pass 2: the same FP32 distances again (bit for bit); survivors are listed first
+      each_point<P>(xf, Xf, N, p, threadIdx.x, KB, [&](float d2f, int i) {
+        if (d2f <= thr) {
+          const uint32_t pos = atomicAdd(&sh_count, 1u);
+          if (pos < (uint32_t)cap) sidx[pos] = i;
+        }
+      });
+      __syncthreads();
+      cnt = (int)sh_count;
+    }
     // then get their exact FP64 distances from the compacted list: a warp instruction of
     // the FP64 pipe serves 32 survivors instead of the few a strided pass would hold
     if (cnt <= cap)

@@ -83,6 +83,25 @@ def test_knn_ties_and_boundary_refinement():
         assert np.array_equal(gpu_knn(X, XX, M), oracle.knn(X, XX, M)), M
 
 
+@pytest.mark.parametrize("near", [True, False])
+def test_knn_when_the_strided_sample_misleads(near):
+    # kernel (a) bounds the ncand-th distance from a sample of the design -- the blocks of
+    # 32 consecutive points that start every 512 points -- and falls back to two full
+    # passes when that bound misses; here the sampled points are either all close to the
+    # locations (too few points under the bound) or all far from them (too many), and the
+    # candidate lists must still equal a full sort's
+    rng = np.random.default_rng(17 + near)
+    N, M = 512 * 10 + 40, 500
+    X = rng.uniform(-1.0, 1.0, size=(N, 2))
+    sampled = np.nonzero((np.arange(N) // 32) % 16 == 0)[0]
+    if near:
+        X[sampled] = rng.uniform(-0.02, 0.02, size=(len(sampled), 2))
+    else:
+        X[sampled] = rng.uniform(5.0, 6.0, size=(len(sampled), 2))
+    XX = rng.uniform(-0.01, 0.01, size=(9, 2))
+    assert np.array_equal(gpu_knn(X, XX, M), oracle.knn(X, XX, M))
+
+
 def test_knn_grid_ties():
     # regular grid design (as in the paper's 201 x 201 illustration): exact ties in d2
     g = np.linspace(-2, 2, 41)
