@@ -107,11 +107,13 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tmp, uint32_t *to
 // (1-based); returns the bin and the count strictly below it.  nbins == HBINS or 256.
 __device__ void find_rank_bin(const uint32_t *hist, int nbins, uint32_t rank, uint32_t *warp_tmp,
                               int *bin_out, uint32_t *below_out) {
-  const int per = nbins / KB > 0 ? nbins / KB : 1;
+  const int per = nbins / KB > 0 ? nbins / KB : 1;  // a power of two
   const int first = threadIdx.x * per;
   uint32_t part = 0;
+  // each thread's range starts at its own rotation: the lanes of a warp read different
+  // banks instead of all `per` apart (a per-way bank conflict)
   if (first < nbins)
-    for (int b = 0; b < per; b++) part += hist[first + b];
+    for (int b = 0; b < per; b++) part += hist[first + ((b + threadIdx.x) & (per - 1))];
   uint32_t total;
   uint32_t pre = block_excl_scan(part, warp_tmp, &total);
   if (first < nbins && pre < rank && rank <= pre + part) {
@@ -338,10 +340,10 @@ __device__ bool bucket_order(const uint32_t *kh, const uint32_t *kl, const int32
   for (int r = threadIdx.x; r < cnt; r += KB) atomicAdd(&bound[bucket_of(r)], 1u);
   __syncthreads();
   // exclusive scan of the counts (nb / KB buckets per thread), flagging an oversized bucket
-  const int per = nb / KB;
+  const int per = nb / KB;  // a power of two
   uint32_t part = 0;
-  for (int k = 0; k < per; k++) {
-    const uint32_t c = bound[threadIdx.x * per + k];
+  for (int k = 0; k < per; k++) {  // rotated start per thread: no bank conflicts
+    const uint32_t c = bound[threadIdx.x * per + ((k + threadIdx.x) & (per - 1))];
     part += c;
     if (c > BUCKET_CAP) *sh_flag = 1u;
   }
