@@ -36,7 +36,7 @@ def test_library_loads_and_exports_every_declared_symbol():
 
 def test_version_and_error_strings():
     assert lagp.lagp_version() >= 100
-    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10):
         assert lagp.strerror(code) and lagp.strerror(code) != "unknown error code"
     assert lagp.strerror(-99) == "unknown error code"
 
@@ -146,3 +146,19 @@ def test_mle_and_stagewise_entry_points_reject_bad_arguments():
     assert L.lagp_select_theta_dev(d, d, 100, 2, d, 1, d, 20, 6, 10, None, 0.0, 0, 0, d, d, None,
                                    None, None, d, 1 << 20, None) == lagp.LAGP_ERR_INVALID_ARG
     assert lagp.strerror(-9).startswith("iteration limit")
+
+
+def test_rescore_count_arguments_on_the_host():
+    # the FP64 and NN forms have no screen to re-score: 0, without touching a workspace;
+    # the mixed screens need the workspace of their call; bad arguments are refused
+    L = lagp.load()
+    out = ctypes.c_int64(-1)
+    assert L.lagp_select_rescore_count(None, 0, 0, 0, ctypes.byref(out), None) == 0 and out.value == 0
+    out.value = -1
+    assert L.lagp_select_rescore_count(None, 0, 2, 1, ctypes.byref(out), None) == 0 and out.value == 0
+    bad = lagp.LAGP_ERR_INVALID_ARG
+    assert L.lagp_select_rescore_count(None, 0, 0, 1, ctypes.byref(out), None) == bad
+    assert L.lagp_select_rescore_count(None, 0, 1, 1, ctypes.byref(out), None) == bad
+    assert L.lagp_select_rescore_count(None, 0, 7, 0, ctypes.byref(out), None) == bad
+    assert L.lagp_select_rescore_count(None, 0, 0, 3, ctypes.byref(out), None) == bad
+    assert L.lagp_select_rescore_count(None, 4096, 0, 0, None, None) == bad

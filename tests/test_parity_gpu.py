@@ -350,3 +350,40 @@ def test_mixed_shared_factor_row_instance_parity():
     w = inputs.random_case(33, 9000, 2, 2, 6, 180, 4000, d=0.2)
     g, infos, bad = run_parity(w, precision="mixed")
     assert not bad, bad[:3]
+
+
+@pytest.mark.parametrize("method", ["alc", "mspe"])
+def test_rescore_count_on_exact_ties(method):
+    # a location at the centre of a symmetric grid: mirror-image candidates have equal
+    # scores, so the mixed screen must hand steps to the FP64 re-score; the count is that
+    # of the last call on the workspace, at most one per location and greedy step, and the
+    # designs still pass the protocol
+    torch = _torch()
+    g1 = np.linspace(-1.0, 1.0, 31)
+    a, b = np.meshgrid(g1, g1, indexing="ij")
+    X = np.stack([a.ravel(), b.ravel()], 1)
+    Z = np.sin(2.0 * X[:, 0]) * np.cos(X[:, 1])
+    XX = np.array([[0.0, 0.0], [1.0 / 30.0, 1.0 / 30.0], [0.5, 0.0], [-1.0 / 3.0, 1.0 / 3.0]])
+    import types
+    w = types.SimpleNamespace(X=X, Z=Z, XX=XX, n0=6, n=30, ncand=200, d=0.1, g=1e-6, T=4, p=2)
+    cand = gpu_knn(X, XX, w.ncand)
+    out = {k: torch.empty(w.T, dtype=torch.float64, device="cuda") for k in ("mean", "s2", "var")}
+    idx = torch.empty((w.T, w.n), dtype=torch.int32, device="cuda")
+    st = torch.empty(w.T, dtype=torch.int8, device="cuda")
+    ws = lagp.workspace(lagp.lagp_select_workspace_bytes(w.T, 2, w.n, w.ncand, method, "mixed"))
+    lagp.lagp_select_dev(dev(X, torch.float64), dev(Z, torch.float64), dev(XX, torch.float64),
+                         dev(cand, torch.int32), w.n0, w.n, w.d, w.g, method, "mixed", out["mean"],
+                         out["s2"], out["var"], idx, st, ws)
+    torch.cuda.synchronize()
+    count = lagp.lagp_select_rescore_count(ws, method, "mixed")
+    assert 1 <= count <= w.T * (w.n - w.n0), count
+    assert lagp.lagp_select_rescore_count(ws, method, "fp64") == 0
+    assert (st.cpu().numpy() == 0).all()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    gi = idx.cpu().numpy()
+    ocand = oracle.knn(X, XX, w.ncand)
+    assert np.array_equal(cand, ocand)
+    for t in range(w.T):
+        info = check_location(w, t, ocand[t], gi[t], g["mean"][t], g["s2"][t], method,
+                              gpu_var=g["var"][t])
+        assert info["ok_vals"], info
