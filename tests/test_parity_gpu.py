@@ -365,7 +365,7 @@ def test_rescore_count_on_exact_ties(method):
     Z = np.sin(2.0 * X[:, 0]) * np.cos(X[:, 1])
     XX = np.array([[0.0, 0.0], [1.0 / 30.0, 1.0 / 30.0], [0.5, 0.0], [-1.0 / 3.0, 1.0 / 3.0]])
     import types
-    w = types.SimpleNamespace(X=X, Z=Z, XX=XX, n0=6, n=30, ncand=200, d=0.1, g=1e-6, T=4, p=2)
+    w = types.SimpleNamespace(X=X, Z=Z, XX=XX, n0=6, n=30, ncand=200, d=0.02, g=1e-6, T=4, p=2)
     cand = gpu_knn(X, XX, w.ncand)
     out = {k: torch.empty(w.T, dtype=torch.float64, device="cuda") for k in ("mean", "s2", "var")}
     idx = torch.empty((w.T, w.n), dtype=torch.int32, device="cuda")
