@@ -21,6 +21,7 @@ namespace {
 
 constexpr float DELTA = 1e-5f;     // near-tie margin for the FP64 re-score
 
+
 constexpr int RESCORE_CAP = 64;    // candidates re-scored per pass
 
 // exp(a) for a <= 0 on a pair, in float-float (Tang's table-driven method with N = 64, see
@@ -210,12 +211,15 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsig
   // the first RA - 1 global rows start on their way (one copy group each); streamed rows
   // do not fit in L2 anyway, so they go evict-first and leave it to the data re-read every
   // step (candidate coordinates; 8-d workload 156.2 -> 140.5 ms)
-  const unsigned long long polf = l2_evict_first_policy();
+  unsigned long long polf = 0;
+  if constexpr (RA > 0) {
+    polf = l2_evict_first_policy();
 #pragma unroll
-  for (int st = 0; st < RA - 1; st++) {
-    if (jr + st < C.j)
-      cp_async16_l2_hint(C.ring + st * nt, C.U + (size_t)(jr + st) * C.Qpad + q, polf);
-    cp_async_commit();
+    for (int st = 0; st < RA - 1; st++) {
+      if (jr + st < C.j)
+        cp_async16_l2_hint(C.ring + st * nt, C.U + (size_t)(jr + st) * C.Qpad + q, polf);
+      cp_async_commit();
+    }
   }
   // squared distance of the pair to the new point
   float2 dh = f2s(0.0f), dl = f2s(0.0f);
@@ -235,15 +239,37 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsig
   const ff2 kc = exp_ff2(ff2{neg2(arg.h), neg2(arg.l)}, C.tabh, C.tabl);   // K(s, c)
   ff2acc acc{kc.h, kc.l};
   // K(s, c) - sum_i u_s[i] u_c[i]: compensated accumulation over the rows held in shared
-  // memory, then over those streamed through the ring
-#pragma unroll 4
-  for (int i = 0; i < jr; i++)
-    ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], C.Us[(size_t)i * C.Qpad + q]);
+  // memory, then over those from global memory (loaded directly, or streamed through the
+  // ring).  Four rows per iteration, written out: a row pointer per stream and the four
+  // loads issued before their terms are accumulated (0.8 % faster than `#pragma unroll 4`
+  // of an indexed loop, with 12 % fewer integer instructions).
+  {
+    const float4 *us = C.Us + q;
+    const int Q = C.Qpad;
+    int i = 0;
+    for (; i + 4 <= jr; i += 4, us += 4 * Q) {
+      const float4 b0 = us[0], b1 = us[Q], b2 = us[2 * Q], b3 = us[3 * Q];
+      ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], b0);
+      ff2acc_sub_prod(acc, C.srow4[i + 1], C.srow2[i + 1], b1);
+      ff2acc_sub_prod(acc, C.srow4[i + 2], C.srow2[i + 2], b2);
+      ff2acc_sub_prod(acc, C.srow4[i + 3], C.srow2[i + 3], b3);
+    }
+    for (; i < jr; i++, us += Q) ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], *us);
+  }
   if constexpr (RA == 0) {
     const unsigned long long pol = l2_evict_last_policy();
-#pragma unroll 4
-    for (int i = jr; i < C.j; i++)
-      ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], ld_l2_hint(C.U + (size_t)i * C.Qpad + q, pol));
+    const float4 *ug = C.U + (size_t)jr * C.Qpad + q;
+    const size_t Q = C.Qpad;
+    int i = jr;
+    for (; i + 4 <= C.j; i += 4, ug += 4 * Q) {
+      const float4 b0 = ld_l2_hint(ug, pol), b1 = ld_l2_hint(ug + Q, pol);
+      const float4 b2 = ld_l2_hint(ug + 2 * Q, pol), b3 = ld_l2_hint(ug + 3 * Q, pol);
+      ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], b0);
+      ff2acc_sub_prod(acc, C.srow4[i + 1], C.srow2[i + 1], b1);
+      ff2acc_sub_prod(acc, C.srow4[i + 2], C.srow2[i + 2], b2);
+      ff2acc_sub_prod(acc, C.srow4[i + 3], C.srow2[i + 3], b3);
+    }
+    for (; i < C.j; i++, ug += Q) ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], ld_l2_hint(ug, pol));
   } else {
     int sc = 0, sp = RA - 1;  // ring stages of rows i and i + RA - 1
     for (int i = jr; i < C.j; i++) {
