@@ -203,9 +203,10 @@ struct StepCtx {
 // RA = 0: the global rows are loaded straight into registers (four in flight); RA > 0:
 // they stream through a ring of RA stages.  The ring pays where the rows come from DRAM
 // (large n x M); where they mostly hit L2 its bookkeeping costs more than it hides.
+// u0, u1: the pair's used flags (read once by the caller).
 template <int RA>
-__device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsigned char *used,
-                                            float &b1, int &r1, float &b2) {
+__device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bool u1, float &b1,
+                                            int &r1, float &b2) {
   const int nt = blockDim.x;
   const int jr = C.j < C.R ? C.j : C.R;  // rows R .. j-1 come from global memory
   // the first RA - 1 global rows start on their way (one copy group each); streamed rows
@@ -283,9 +284,17 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, const unsig
       ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], b);
     }
   }
-  const bool u0 = used[2 * q], u1 = used[2 * q + 1];
   const ff2 u = ff2_mul(ff2acc_result(acc), C.inv2);               // u_c[j]
-  ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
+  if constexpr (RA == 0) {
+    // the same for the whole CTA: a shared or a global store instead of a generic one
+    // (paper-2d 13.93 -> 13.64 ms with the flags read once; slower with the row ring)
+    if (C.j < C.R)
+      ff2_store(C.Us + C.j * C.Qpad + q, u);
+    else
+      ff2_store(C.U + (size_t)C.j * C.Qpad + q, u);
+  } else {
+    ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
+  }
   const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
   ff2 v = ff2_sub(v0, ff2_mul(u, u));
   ff2 cx = ff2_sub(c0, ff2_mul(C.uxj2, u));

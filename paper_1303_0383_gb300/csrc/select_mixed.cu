@@ -269,8 +269,9 @@ __global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixPara
       const StepCtx C{U, Us, R, ring, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2,
                       Qpad, p, j, 2 * q0, want};
       for (int q = tid; q < Qs; q += MB) {
-        if (used[2 * q] && used[2 * q + 1]) continue;
-        screen_pair<RA>(C, q, used, b1, r1, b2);
+        const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+        if (u0 && u1) continue;
+        screen_pair<RA>(C, q, u0, u1, b1, r1, b2);
       }
       // best and second-best screen scores: warp shuffles, one barrier, then every
       // thread merges the per-warp results itself (double-buffered by step parity)
