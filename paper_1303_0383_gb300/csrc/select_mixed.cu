@@ -70,6 +70,15 @@ struct MixParams {
 #ifndef LAGP_MIX_MINB
 #define LAGP_MIX_MINB LAGP_MIX_CTAS_PER_SM  // 3 CTAs per SM, each with its first factor rows in shared memory
 #endif
+// The row-ring instances (one CTA per location) run up to 4 CTAs per SM: their rows come
+// from DRAM, and more warps in flight hide more of that (8-d workload, the shared-row-copy
+// instance at 4 CTAs per SM: 138.7 -> 133.1 ms).  At 4 CTAs per SM the instance without
+// the ring was slower (paper-2d 13.58 -> 15.25 ms: 3 rows in shared memory instead of 5).
+constexpr int kRingMinB = 4;
+__host__ __device__ constexpr int mix_minb(int RA, bool SR, bool CLU) {
+  (void)SR;
+  return (RA > 0 && !CLU) ? kRingMinB : LAGP_MIX_MINB;
+}
 // RA: stages of the row ring (0: none).  SR: one shared copy of the step's factor row for
 // the whole CTA (one more block barrier per step) instead of one per warp, which frees
 // (MB/32 - 1) row copies of shared memory for the ring on large designs.
@@ -81,7 +90,7 @@ struct MixParams {
 // 1/CL of the locations in flight, the live factor rows shrink by CL and more of each
 // CTA's rows fit in shared memory.  Every candidate's arithmetic is the same in both forms.
 template <int RA, bool SR, bool CLU>
-__global__ void __launch_bounds__(MB, LAGP_MIX_MINB) select_mixed_kernel(MixParams P) {
+__global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel(MixParams P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, nmax = P.nmax;
   constexpr int NW = SR ? 1 : MB / 32;                       // copies of the factor row
@@ -430,10 +439,13 @@ size_t mix_static_smem(MixVariant v) {
   return cudaFuncGetAttributes(&fa, mix_kernel(v)) == cudaSuccess ? fa.sharedSizeBytes : 4096;
 }
 
+int mix_minb(MixVariant v) { return mix_minb(v.RA, v.SR, v.CL > 1); }
+
 size_t mix_resident(int Qpad, int n, MixVariant v, const DevInfo &di) {
   const size_t per = mix_static_smem(v) + 1024 + mix_smem_bytes(Qpad, n, 0, v.RA, v.SR);
   const size_t k = di.smem_per_sm / per;  // 1 KB reserved per CTA
-  return k < (size_t)LAGP_MIX_MINB ? k : (size_t)LAGP_MIX_MINB;
+  const size_t mb = (size_t)mix_minb(v);
+  return k < mb ? k : mb;
 }
 
 // Launch-shape overrides for measurements (they change no result): LAGP_MIX_CLUSTER = CTAs
@@ -455,9 +467,10 @@ int mix_cluster_size(int n, int M) {
 
 // The row ring is used where a CTA's factor rows (n x M float-float entries) come mostly
 // from DRAM -- 8-d workload (n = 100, M = 2000) yes, paper-2d (n = 50, M = 1000) no, both
-// measured -- and only if its shared memory leaves as many CTAs resident per SM; where the
-// per-warp row copies are what leave no room (large n, the batched workload), with one
-// shared copy.  The cluster form has no shared-copy instance.
+// measured -- and only if its shared memory leaves at least as many CTAs resident per SM;
+// with one shared copy of the factor row where the per-warp copies are what leave no room
+// (the 8-d workload at 4 CTAs per SM, the batched workload's large n).  The cluster form has
+// no shared-copy instance.
 MixVariant mix_variant(int n, int M, int CL, const DevInfo &di) {
   const int Qpad = mix_qpad(M, CL);
   const MixVariant plain{0, false, CL}, ring{RING_A, false, CL}, ring_sr{RING_A, true, CL};
@@ -465,18 +478,22 @@ MixVariant mix_variant(int n, int M, int CL, const DevInfo &di) {
   if (er == 0) return plain;
   if (er == 1) return ring;
   if ((int64_t)n * M < 100000 * (int64_t)CL) return plain;
+  // the most resident CTAs per SM wins; at a tie, the ring with per-warp row copies (no
+  // extra barrier per step)
   const size_t k0 = mix_resident(Qpad, n, plain, di);
-  if (mix_resident(Qpad, n, ring, di) >= k0) return ring;
-  if (CL == 1 && mix_resident(Qpad, n, ring_sr, di) >= k0) return ring_sr;
+  const size_t kr = mix_resident(Qpad, n, ring, di);
+  const size_t ks = CL == 1 ? mix_resident(Qpad, n, ring_sr, di) : 0;
+  if (kr >= k0 && kr >= ks) return ring;
+  if (ks >= k0) return ring_sr;
   return plain;
 }
 
-// Factor rows kept in shared memory: as many as LAGP_MIX_MINB resident CTAs per SM leave
+// Factor rows kept in shared memory: as many as the instance's resident CTAs per SM leave
 // room for (the rest stream from L2).  Row i is read at every step after step i, so the
 // first rows carry the most traffic.
 int mix_rows_in_smem(int Qpad, int n, MixVariant v, const DevInfo &di) {
   const size_t stat = mix_static_smem(v);
-  size_t per_cta = di.smem_per_sm / LAGP_MIX_MINB;
+  size_t per_cta = di.smem_per_sm / mix_minb(v);
   const size_t fixed = stat + 1024 + mix_smem_bytes(Qpad, n, 0, v.RA, v.SR);  // 1 KB reserved per CTA
   if (per_cta > di.smem_optin) per_cta = di.smem_optin;
   if (per_cta <= fixed) return 0;
@@ -485,10 +502,11 @@ int mix_rows_in_smem(int Qpad, int n, MixVariant v, const DevInfo &di) {
   return (int)(r < (size_t)n ? r : (size_t)n);
 }
 
-// CTAs of a uniform launch: LAGP_MIX_MINB per SM (one location each), or in the cluster
-// form as many clusters of CL as can be resident at once (at most one per location).
-int mix_grid(int64_t T, int num_sms) {
-  int64_t g = (int64_t)num_sms * LAGP_MIX_MINB;
+// CTAs of a uniform launch: the instance's resident CTAs per SM (one location each), or in
+// the cluster form as many clusters of CL as can be resident at once (at most one per
+// location).
+int mix_grid(int64_t T, int num_sms, MixVariant v) {
+  int64_t g = (int64_t)num_sms * mix_minb(v);
   return (int)(T < g ? (T > 0 ? T : 1) : g);
 }
 
@@ -534,12 +552,12 @@ MixLayout mix_layout(int G, int p, int n, int Qpad, int64_t T, int64_t idx_total
   return L;
 }
 
-// The workspace of a uniform launch covers every cluster size (the grid of CL CTAs per
-// location has at most min(LAGP_MIX_MINB x SMs, CL x T) CTAs).
+// The workspace of a uniform launch covers every instance and cluster size (the grid has
+// at most min(resident CTAs per SM x SMs, CL x T) CTAs).
 size_t mix_uniform_bytes(int64_t T, int p, int n, int M, int num_sms) {
   size_t best = 0;
   for (int CL = 1; CL <= kMaxCL; CL *= 2) {
-    int64_t G = (int64_t)num_sms * LAGP_MIX_MINB;
+    int64_t G = (int64_t)num_sms * (CL == 1 ? kRingMinB : LAGP_MIX_MINB);
     const int64_t cap = (int64_t)CL * (T > 0 ? T : 1);
     G = G < cap ? G : cap;
     const size_t b = mix_layout((int)G, p, n, mix_qpad(M, CL), T, T * n, num_sms).total;
@@ -627,7 +645,7 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   if (st) return st;
   const MixVariant v = mix_variant(a.n, a.M, mix_cluster_size(a.n, a.M), di);
   const int Qpad = mix_qpad(a.M, v.CL);
-  int G = mix_grid(a.T, di.num_sms);
+  int G = mix_grid(a.T, di.num_sms, v);
   if (v.CL > 1) {
     const int R = mix_rows_in_smem(Qpad, a.n, v, di);
     st = mix_cluster_grid(a.T, v, mix_smem_bytes(Qpad, a.n, R, v.RA, v.SR), di.num_sms, &G);
