@@ -135,6 +135,24 @@ def paper_form_flops_per_location(n0, n, M):
     return float(sum(2 * j * j * (M - j) for j in range(n0, n)))
 
 
+def dense_flops_per_location(n0, n, M, p):
+    """Algorithmic FP64 flops of the paper's explicit-inverse form (lagp_select_dense_dev)
+    for one location: every pool candidate at a greedy step with j design points costs
+    j(j+1) (the quadratic form k_j(c)^T K_j^{-1} k_j(c) over the upper triangle, FMA = 2)
+    + 2j (its dot with K_j^{-1} k_j(x)) + 4 (v, cov, score); every step adds 6j^2 (K_j^{-1}
+    k_j(x), K_j^{-1} k_j(s) and the partition inverse update) and, but for the last,
+    3p + 1 + EXP_FLOPS per candidate for the new point's correlations; plus 3p + 1 +
+    EXP_FLOPS per candidate for K(x, c) at the start."""
+    total = M * (3 * p + 1 + EXP_FLOPS)
+    for j in range(n):
+        if j >= n0:
+            total += (M - j) * (j * (j + 1) + 2 * j + 4)
+        total += 6 * j * j
+        if j + 1 < n:
+            total += M * (3 * p + 1 + EXP_FLOPS)
+    return float(total)
+
+
 def mspe_flops_per_location(n0, n, M, p):
     """Algorithmic FP64 flops of the MSPE design in the Cholesky basis for one location:
     every pool candidate at step j costs 6j (three j-dots: u_c, its derivative row and the
@@ -719,6 +737,8 @@ def run_gpu(args):
             elif name == "batched":
                 line["batched"] = {prec: measure_batched(args, prec, xs, xw, args.batch_T)
                                    for prec in ("mixed", "fp64")}
+            elif name == "dense":
+                line["dense_ab"] = dense_ab_pair(10000, 1000, 3, 3)
             elif name == "serving":
                 line["serving"] = measure_serving([float(r) for r in args.extra_serve_rates.split(",")],
                                                   args.extra_serve_seconds, ["mixed", "fp64"])
@@ -726,6 +746,111 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure_dense_ab(wname, T_sub, steps, warmup):
+    """The A/B of the two forms of ALC on one workload's first T_sub locations, candidate
+    lists computed once: kernels (b)+(c) of the paper's explicit-inverse form
+    (lagp_select_dense_dev, O(j^2) per candidate) against the Cholesky-row kernels
+    (lagp_select_dev, O(j)), FP64 and mixed, each timed with CUDA events over `steps`
+    launches after `warmup` (L2 flushed between launches).  Agreement of the paper form's
+    designs with the exact greedy designs (the Cholesky-row FP64 kernel's, which the parity
+    tests pin to the oracle), and the paper form's roofline against the FP64 pipe."""
+    import torch
+    from paper_1303_0383_gb300 import lagp
+    w = _workloads()[wname]["make"]()
+    w.XX = np.ascontiguousarray(w.XX[:T_sub])
+    T, M, dev = w.T, w.ncand, torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    X, Z, XX = (torch.as_tensor(a).to(dev) for a in (w.X, w.Z, w.XX))
+    cand = torch.empty((T, M), dtype=torch.int32, device=dev)
+    lagp.lagp_knn_dev(X, XX, M, cand, lagp.workspace(lagp.lagp_knn_workspace_bytes(w.N, T, M), dev),
+                      stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    sampler = ClockSampler(int(vis) if vis.isdigit() else torch.cuda.current_device())
+    sampler.start()
+    res = {}
+    for key in ("dense", "fp64", "mixed"):
+        mean = torch.empty(T, dtype=torch.float64, device=dev)
+        s2, var = torch.empty_like(mean), torch.empty_like(mean)
+        idx = torch.empty((T, w.n), dtype=torch.int32, device=dev)
+        status = torch.empty(T, dtype=torch.int8, device=dev)
+        if key == "dense":
+            ws = lagp.workspace(lagp.lagp_select_dense_workspace_bytes(T, w.p, w.n, M), dev)
+            run = lambda: lagp.lagp_select_dense_dev(X, Z, XX, cand, w.n0, w.n, w.d, w.g, mean, s2,
+                                                     var, idx, status, ws, stream)
+        else:
+            ws = lagp.workspace(lagp.lagp_select_workspace_bytes(T, w.p, w.n, M, "alc", key), dev)
+            run = (lambda k=key: lagp.lagp_select_dev(X, Z, XX, cand, w.n0, w.n, w.d, w.g, "alc", k,
+                                                      mean, s2, var, idx, status, ws, stream))
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            flush.add_(1.0)
+            a.record(stream)
+            run()
+            b.record(stream)
+        torch.cuda.synchronize()
+        res[key] = dict(ms=sum(a.elapsed_time(b) for a, b in evs) / steps,
+                        idx=idx.cpu().numpy(), s2=s2.cpu().numpy(),
+                        failed=int((status != 0).sum()))
+    clocks = sampler.stop()
+    d, f = res["dense"], res["fp64"]
+    same = (d["idx"] == f["idx"]).all(axis=1)
+    overlap = np.array([len(np.intersect1d(a, b)) / w.n for a, b in zip(d["idx"], f["idx"])])
+    first = np.array([int(np.argmax(a != b)) if (a != b).any() else w.n
+                      for a, b in zip(d["idx"], f["idx"])])
+    ratio = d["s2"] / f["s2"]
+    alg = dense_flops_per_location(w.n0, w.n, M, w.p)
+    achieved = alg * T / (d["ms"] / 1e3) / 1e12
+    return {
+        "workload": w.name, "T": T, "n0": w.n0, "n": w.n, "ncand": M, "g": w.g,
+        "steps": steps, "warmup": warmup, "l2": "flushed between timed launches (256 MB write)",
+        "ms": {"dense_fp64": d["ms"], "cholesky_row_fp64": f["ms"], "cholesky_row_mixed": res["mixed"]["ms"]},
+        "dense_over_cholesky_row_fp64": d["ms"] / f["ms"],
+        "dense_over_cholesky_row_mixed": d["ms"] / res["mixed"]["ms"],
+        "failed_locations": {k: r["failed"] for k, r in res.items()},
+        "dense_designs": {
+            "equal_to_exact_greedy": float(same.mean()),
+            "mean_overlap_with_exact_greedy": float(overlap.mean()),
+            "median_first_differing_step": float(np.median(first[~same])) if (~same).any() else None,
+            "s2_ratio_to_exact_greedy": {"median": float(np.median(ratio)),
+                                         "p99": float(np.quantile(ratio, 0.99)),
+                                         "max": float(ratio.max()), "min": float(ratio.min())}},
+        "roofline": {"kernel": "select_dense_kernel (kernels b+c)", "bound": "alu",
+                     "achieved": achieved, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS_DERIVED,
+                     "frac": achieved / FP64_PEAK_TFLOPS_DERIVED, "work_per_location": alg,
+                     "work_unit": "FP64 flops of the paper's explicit-inverse form (FMA = 2, exp = 20)",
+                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+        "clocks": clocks,
+    }
+
+
+def dense_ab_pair(T2, T8, steps, warmup):
+    """The A/B of the two forms on paper-2d (first T2 locations) and smooth-8d (first T8)."""
+    return {"paper-2d": measure_dense_ab("paper-2d", T2, steps, warmup),
+            "smooth-8d": measure_dense_ab("smooth-8d", T8, steps, warmup)}
+
+
+def run_dense_ab(args):
+    """--workload dense-ab: the A/B of the paper's explicit-inverse form against the
+    Cholesky-row kernels alone, one JSON line (rank 0 of one GPU; --locations caps both
+    workloads' location counts)."""
+    from paper_1303_0383_gb300 import lagp
+    lagp.load()
+    T2 = args.locations or 10000
+    T8 = min(args.locations or 1000, 1000)
+    ab = dense_ab_pair(T2, T8, args.steps, args.warmup)
+    print(json.dumps({"metric": "ALC kernels (b)+(c) ms: the paper's explicit-inverse form vs the "
+                                "Cholesky-row form", "unit": "ms", "higher_is_better": False,
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f64 (paper form) / f64 and f32x2+f64 (Cholesky-row)",
+                      "data": "synthetic", "dense_ab": ab}), flush=True)
     return 0
 
 
@@ -945,8 +1070,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--workload", default="paper-2d",
                     choices=["paper-2d", "smooth-8d", "grid-2d", "borehole", "borehole-8000", "batched",
-                             "serving"])
-    ap.add_argument("--extras", default="smooth-8d,batched,serving",
+                             "serving", "dense-ab"])
+    ap.add_argument("--extras", default="smooth-8d,batched,dense,serving",
                     help="other workloads measured after the default paper-2d line and added to it "
                          "as keys (comma list; empty: none)")
     ap.add_argument("--no-extras", dest="extras", action="store_const", const="")
@@ -966,6 +1091,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "dense-ab":
+        return run_dense_ab(args)
     return run_gpu(args)
 
 

@@ -135,6 +135,27 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
                     double *s2, double *var, int32_t *idx, int8_t *status, void *workspace,
                     size_t workspace_bytes, void *stream);
 
+/* Scratch bytes lagp_select_dense_dev needs. */
+size_t lagp_select_dense_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand);
+
+/* ALC in the paper's own form, the comparison for lagp_select_dev (Sec. 3.2; SM "Partition
+ * inverse equations"): each location keeps K_j^{-1} explicitly and grows it by the
+ * partition inverse equations; each step scores every candidate by Eq. dxy from K_j^{-1},
+ * O(j^2) per candidate (the quadratic form k_j(c)^T K_j^{-1} k_j(c)) where lagp_select_dev
+ * takes O(j).  FP64 throughout.  The explicit inverse carries errors of order
+ * cond(K_j) eps into v_j(c) = K(c,c) - k_j(c)^T K_j^{-1} k_j(c), so with small nuggets
+ * the choices can differ from the exact greedy design that lagp_select_dev returns; the
+ * outputs are the predictive equations on the design this call chose (FP64 Cholesky, as
+ * lagp_design_predict_dev).  Arguments and outputs as lagp_select_dev with method ALC and
+ * precision FP64; n > 128 returns LAGP_ERR_UNSUPPORTED (K_j^{-1} lives in shared memory).
+ * A location where no candidate keeps a positive v_j(c) gets NaN outputs, idx -1 and
+ * status LAGP_ERR_NOT_PD. */
+int lagp_select_dense_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                          const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                          int32_t n0, int32_t n, double theta, double g, double *mean, double *s2,
+                          double *var, int32_t *idx, int8_t *status, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
 /* Diagnostics of the mixed-precision screens (Sec. 3.3 decisions; no counterpart in the
  * paper): the number of FP64 re-score passes -- steps of some location at which the screen's
  * best scores were near-tied (or, for MSPE, G or J was a cancellation beyond the screen's

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblagp.so")
-SOURCES = ["api.cu", "knn.cu", "select.cu", "noalloc.cu", "fp64_exp.cu", "select_mixed.cu", "select_mspe.cu", "select_mspe_mixed.cu", "batch.cu", "server.cu", "predict.cu", "mle.cu"]
+SOURCES = ["api.cu", "knn.cu", "select.cu", "noalloc.cu", "fp64_exp.cu", "select_mixed.cu", "select_dense.cu", "select_mspe.cu", "select_mspe_mixed.cu", "batch.cu", "server.cu", "predict.cu", "mle.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

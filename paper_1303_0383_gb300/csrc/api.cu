@@ -213,6 +213,31 @@ int lagp_select_dev(const double *X, const double *Z, int64_t N, int32_t p, cons
   return select_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
+size_t lagp_select_dense_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand) {
+  DevInfo di;
+  if (dev_info(&di)) return 0;
+  return select_dense_workspace_bytes(T, p, n, ncand, di.num_sms);
+}
+
+int lagp_select_dense_dev(const double *X, const double *Z, int64_t N, int32_t p,
+                          const double *XX, int64_t T, const int32_t *cand, int32_t ncand,
+                          int32_t n0, int32_t n, double theta, double g, double *mean, double *s2,
+                          double *var, int32_t *idx, int8_t *status, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+  int st = check_common(N, p, T, n0, n, ncand, theta, g, LAGP_ALC, LAGP_FP64);
+  if (st) return st;
+  if (n > select_dense_max_n()) return LAGP_ERR_UNSUPPORTED;
+  if (T > 0 && (!X || !Z || !XX || !cand || !mean || !s2 || !workspace)) return LAGP_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return LAGP_ERR_INVALID_ARG;
+  SelectArgs a;
+  a.X = X; a.Z = Z; a.N = N; a.p = p; a.XX = XX; a.T = T; a.cand = cand;
+  a.M = ncand; a.n0 = n0; a.n = n; a.theta = theta; a.g = g; a.theta_loc = nullptr;
+  a.start = nullptr; a.nstart = 0; a.r_min = 0.0; a.n_out = nullptr;
+  a.method = LAGP_ALC; a.precision = LAGP_FP64;
+  a.mean = mean; a.s2 = s2; a.var = var; a.idx = idx; a.status = status;
+  return select_dense_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
 int lagp_select_rescore_count(const void *workspace, size_t workspace_bytes, int32_t method,
                               int32_t precision, int64_t *count, void *stream) {
   if (!count) return LAGP_ERR_INVALID_ARG;

@@ -72,6 +72,12 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
 size_t select_mixed_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
 int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+// ALC in the paper's own form (explicit K_j^{-1}, partition inverse updates), FP64:
+// kernel (b) then kernel (c) on the selected design (select_dense.cu).
+int select_dense_max_n();
+size_t select_dense_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms);
+int select_dense_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t stream);
+
 // Kernel (c) on a selected design: FP64 predictive equations for every location from its
 // design indices (idx < 0 marks a location whose screen failed).
 struct PredictArgs {

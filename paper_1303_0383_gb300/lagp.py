@@ -65,6 +65,10 @@ def load(path: str | None = None):
     L.lagp_select_workspace_bytes.restype = sz
     L.lagp_select_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64, i32, i32,
                                   P, P, P, P, P, P, sz, P]
+    L.lagp_select_dense_workspace_bytes.argtypes = [i64, i32, i32, i32]
+    L.lagp_select_dense_workspace_bytes.restype = sz
+    L.lagp_select_dense_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64, P, P,
+                                        P, P, P, P, sz, P]
     L.lagp_select_rescore_count.argtypes = [P, sz, i32, i32, ctypes.POINTER(i64), P]
     L.lagp_predict_workspace_bytes.argtypes = [i64, i64, i32, i32, i32, i32, i32]
     L.lagp_predict_workspace_bytes.restype = sz
@@ -183,6 +187,22 @@ def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2
                                 _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
                                 _dp(status), _dp(ws), ws.numel(), _stream(stream)),
          "lagp_select_dev")
+
+
+def lagp_select_dense_workspace_bytes(T, p, n, ncand) -> int:
+    return int(load().lagp_select_dense_workspace_bytes(T, p, n, ncand))
+
+
+def lagp_select_dense_dev(X, Z, XX, cand, n0, n, theta, g, mean, s2, var=None, idx=None,
+                          status=None, ws=None, stream=None) -> None:
+    """ALC in the paper's own form (explicit K_j^{-1}, O(j^2) per candidate), FP64, on
+    device tensors, candidate lists given; outputs as lagp_select_dev."""
+    N, p = X.shape
+    T, M = cand.shape
+    _chk(load().lagp_select_dense_dev(_dp(X), _dp(Z), N, p, _dp(XX), T, _dp(cand), M, n0, n,
+                                      theta, g, _dp(mean), _dp(s2), _dp(var), _dp(idx),
+                                      _dp(status), _dp(ws), ws.numel(), _stream(stream)),
+         "lagp_select_dense_dev")
 
 
 def lagp_select_rescore_count(ws, method="alc", precision="mixed", stream=None) -> int:

@@ -162,3 +162,26 @@ def test_rescore_count_arguments_on_the_host():
     assert L.lagp_select_rescore_count(None, 0, 7, 0, ctypes.byref(out), None) == bad
     assert L.lagp_select_rescore_count(None, 0, 0, 3, ctypes.byref(out), None) == bad
     assert L.lagp_select_rescore_count(None, 4096, 0, 0, None, None) == bad
+
+
+def test_dense_form_arguments_on_the_host():
+    # the paper's explicit-inverse form shares lagp_select_dev's rules, keeps K_j^{-1} in
+    # shared memory (n <= 128) and needs a 256-byte aligned workspace
+    L = lagp.load()
+    P = ctypes.c_void_p
+    d = P(256)
+
+    def call(**kw):
+        a = dict(N=100, p=2, T=4, M=50, n0=6, n=20, theta=0.5, g=1e-6, X=d, ws=d)
+        a.update(kw)
+        return L.lagp_select_dense_dev(a["X"], d, a["N"], a["p"], d, a["T"], d, a["M"], a["n0"],
+                                       a["n"], a["theta"], a["g"], d, d, None, None, None,
+                                       a["ws"], 1 << 20, None)
+    bad = lagp.LAGP_ERR_INVALID_ARG
+    assert call(n0=0) == bad and call(n=2) == bad and call(M=19) == bad and call(p=9) == bad
+    assert call(theta=0.0) == bad and call(g=-1.0) == bad and call(X=None) == bad
+    assert call(ws=P(8)) == bad
+    assert call(n=129, M=200, N=300) == lagp.LAGP_ERR_UNSUPPORTED
+    # T = 0 does nothing and needs no buffers
+    assert L.lagp_select_dense_dev(None, None, 100, 2, None, 0, None, 50, 6, 20, 0.5, 1e-6, None,
+                                   None, None, None, None, None, 0, None) == 0
