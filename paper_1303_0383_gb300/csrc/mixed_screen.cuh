@@ -180,6 +180,42 @@ __device__ __forceinline__ float4 ld_l2_hint(const float4 *a, unsigned long long
   return v;
 }
 
+// Tensor memory as a second on-chip store for factor rows (no tensor-core work): a CTA
+// allocates 128 columns of its SM's tensor memory; warp w may address only the 32 lanes of
+// its sub-partition, 32 (w & 3) .. 32 (w & 3) + 31, and takes columns 64 (w >> 2) .. + 63 of
+// them, so every thread owns 64 32-bit words of its own lane.  Loads and stores are
+// warp-collective (every lane of the warp executes them with the same address).  The load's
+// wait is tied to the registers it delivers, so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t ta, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&v)[16]) {
+  tmem_ld16_issue(ta, v);
+  tmem_wait16(v);
+}
+__device__ __forceinline__ void tmem_st4(uint32_t ta, float4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta),
+               "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+               "r"(__float_as_uint(v.w))
+               : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+constexpr int kTmemCols = 128;  // columns per CTA (at most 3 CTAs per SM hold 384 of 512)
+
 // One step of the screen for one candidate pair of this thread (Sec. 3.2 update, in
 // float-float): K(s, c) from the squared distance, the new factor entry
 // u_c[j] = (K(s, c) - u_s . u_c) / L_jj, then v_{j+1}(c) = v_j(c) - u_c[j]^2,
@@ -198,17 +234,25 @@ struct StepCtx {
   int Qpad, p, j;
   int c0;        // global rank of the first candidate held here
   bool want;
+  uint32_t tb;   // tensor-memory instance: this thread's first column (lane and column fields)
+  int RT;        // rows R .. R + RT - 1 also held there (a read copy), RT words x 4 per pair
 };
 
 // RA = 0: the global rows are loaded straight into registers (four in flight); RA > 0:
 // they stream through a ring of RA stages.  The ring pays where the rows come from DRAM
 // (large n x M); where they mostly hit L2 its bookkeeping costs more than it hides.
 // u0, u1: the pair's used flags (read once by the caller).
-template <int RA>
+// TM (instance without the ring): rows R .. R + RT - 1 are read from this thread's
+// tensor-memory words instead of L2 (they are still written to global memory, where the
+// step's pivot row is gathered from); the caller keeps every warp convergent.
+template <int RA, bool TM = false>
 __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bool u1, float &b1,
                                             int &r1, float &b2) {
   const int nt = blockDim.x;
   const int jr = C.j < C.R ? C.j : C.R;  // rows R .. j-1 come from global memory
+  // with tensor memory: rows R .. jt-1 from there, jt .. j-1 from global memory
+  const int jt = TM ? max(jr, min(C.j, C.R + C.RT)) : jr;
+  const uint32_t ta = TM ? C.tb + (uint32_t)((q / nt) * C.RT * 4) : 0u;
   // the first RA - 1 global rows start on their way (one copy group each); streamed rows
   // do not fit in L2 anyway, so they go evict-first and leave it to the data re-read every
   // step (candidate coordinates; 8-d workload 156.2 -> 140.5 ms)
@@ -257,11 +301,26 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
     }
     for (; i < jr; i++, us += Q) ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], *us);
   }
+  if constexpr (TM) {
+    // four rows per load, each waited for before use: issuing the first load ahead of the
+    // shared-memory rows instead keeps its 16 registers live there and spills (13.56 ->
+    // 13.90 ms on paper-2d)
+    for (int i = jr; i < jt; i += 4) {  // rows past jt are loaded but not used
+      uint32_t tw[16];
+      tmem_ld16(ta + (uint32_t)(4 * (i - C.R)), tw);
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (i + k < jt)
+          ff2acc_sub_prod(acc, C.srow4[i + k], C.srow2[i + k],
+                          make_float4(__uint_as_float(tw[4 * k]), __uint_as_float(tw[4 * k + 1]),
+                                      __uint_as_float(tw[4 * k + 2]), __uint_as_float(tw[4 * k + 3])));
+    }
+  }
   if constexpr (RA == 0) {
     const unsigned long long pol = l2_evict_last_policy();
-    const float4 *ug = C.U + (size_t)jr * C.Qpad + q;
+    const float4 *ug = C.U + (size_t)jt * C.Qpad + q;
     const size_t Q = C.Qpad;
-    int i = jr;
+    int i = jt;
     for (; i + 4 <= C.j; i += 4, ug += 4 * Q) {
       const float4 b0 = ld_l2_hint(ug, pol), b1 = ld_l2_hint(ug + Q, pol);
       const float4 b2 = ld_l2_hint(ug + 2 * Q, pol), b3 = ld_l2_hint(ug + 3 * Q, pol);
@@ -288,10 +347,13 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
   if constexpr (RA == 0) {
     // the same for the whole CTA: a shared or a global store instead of a generic one
     // (paper-2d 13.93 -> 13.64 ms with the flags read once; slower with the row ring)
-    if (C.j < C.R)
+    if (C.j < C.R) {
       ff2_store(C.Us + C.j * C.Qpad + q, u);
-    else
+    } else {
       ff2_store(C.U + (size_t)C.j * C.Qpad + q, u);
+      if constexpr (TM)
+        if (C.j < C.R + C.RT) tmem_st4(ta + (uint32_t)(4 * (C.j - C.R)), make_float4(u.h.x, u.h.y, u.l.x, u.l.y));
+    }
   } else {
     ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
   }

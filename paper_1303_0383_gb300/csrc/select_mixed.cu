@@ -65,6 +65,7 @@ struct MixParams {
   int8_t *status;
   int fuse_pred;         // 1: the predictive equations here (matrix in shared memory)
   int CL;                // CTAs per cluster (cluster form): they share one location
+  int RT;                // tensor-memory instance: rows R .. R + RT - 1 also in tensor memory
 };
 
 #ifndef LAGP_MIX_MINB
@@ -82,6 +83,11 @@ __host__ __device__ constexpr int mix_minb(int RA, bool SR, bool CLU) {
 // RA: stages of the row ring (0: none).  SR: one shared copy of the step's factor row for
 // the whole CTA (one more block barrier per step) instead of one per warp, which frees
 // (MB/32 - 1) row copies of shared memory for the ring on large designs.
+// TM: rows R .. R + RT - 1 of each candidate are also kept in the CTA's tensor memory (128
+// columns: RT = 16, 8 or 4 rows for 1, 2 or up to 4 pairs per thread) and the screen reads
+// them from there instead of L2 (GB300, 24 warps per SM, four 16-byte loads per thread:
+// about 200 cycles from tensor memory against about 580 for L2 hits).  Instance without the
+// ring and outside the cluster form only.
 // CLU: the cluster form.  The P.CL CTAs of a thread-block cluster share one location, CTA
 // `crank` holding the candidate pairs crank*Qc .. crank*Qc + Qc - 1 (its own v, cov, flags,
 // factor rows and coordinates); a step's pivot state -- v_j(s), cov_j(x,s), u_s and x_s -- is
@@ -89,8 +95,9 @@ __host__ __device__ constexpr int mix_minb(int RA, bool SR, bool CLU) {
 // and the per-warp best scores are merged over the cluster after one cluster barrier.  With
 // 1/CL of the locations in flight, the live factor rows shrink by CL and more of each
 // CTA's rows fit in shared memory.  Every candidate's arithmetic is the same in both forms.
-template <int RA, bool SR, bool CLU>
+template <int RA, bool SR, bool CLU, bool TM = false>
 __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel(MixParams P) {
+  static_assert(!TM || (RA == 0 && !CLU), "tensor-memory rows: instance without ring or cluster");
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, nmax = P.nmax;
   constexpr int NW = SR ? 1 : MB / 32;                       // copies of the factor row
@@ -118,6 +125,21 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
   __shared__ double red_n[MB / 32], red_d[MB / 32];
   __shared__ int red_rr[MB / 32];
   __shared__ int sh_loc, sh_fail, sh_nlist;
+  __shared__ uint32_t sh_tmem;
+  if constexpr (TM) {
+    // 128 columns of this SM's tensor memory (at most 3 CTAs per SM: 384 of 512, so the
+    // allocation never waits), released at the end of the kernel
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&sh_tmem)),
+                   "n"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
   if (threadIdx.x < 64) {
     tabh[threadIdx.x] = c_exp.tabf_h[threadIdx.x];
     tabl[threadIdx.x] = c_exp.tabf_l[threadIdx.x];
@@ -131,6 +153,9 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
   float4 *Xr = P.Xr + (size_t)blockIdx.x * P.pmax * Qpad;
   const int lda = nmax + 2;
   double *A = P.A + (size_t)blockIdx.x * nmax * lda;
+  // this thread's tensor-memory words: its warp's lane quarter, its half of the columns
+  const uint32_t tb = TM ? sh_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2))
+                         : 0u;
   float4 *srow4 = wrow4 + (SR ? 0 : warp) * nrow;  // this warp's copy of the new factor row
   float2 *srow2 = wrow2 + (SR ? 0 : warp) * nrow;
   float2 *sxs = wxs + (SR ? 0 : warp) * kMaxP;     // and of the new point's coordinates
@@ -276,11 +301,23 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
       float b1 = -1.0f, b2 = -1.0f;
       int r1 = 0x7fffffff;
       const StepCtx C{U, Us, R, ring, Xr, vp, cp, srow4, srow2, sxs, tabh, tabl, inv2, uxj2,
-                      Qpad, p, j, 2 * q0, want};
-      for (int q = tid; q < Qs; q += MB) {
-        const bool u0 = used[2 * q], u1 = used[2 * q + 1];
-        if (u0 && u1) continue;
-        screen_pair<RA>(C, q, u0, u1, b1, r1, b2);
+                      Qpad, p, j, 2 * q0, want, tb, TM ? P.RT : 0};
+      if constexpr (TM) {
+        // whole warps (tensor-memory accesses are warp-collective): pairs up to the next
+        // multiple of 32 (all within Qpad; those past Qs only update state nobody reads),
+        // a pair skipped only when the whole warp's are used
+        const int Q32 = (Qs + 31) & ~31;
+        for (int q = tid; q < Q32; q += MB) {
+          const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+          if (__all_sync(0xffffffffu, u0 && u1)) continue;
+          screen_pair<RA, true>(C, q, u0, u1, b1, r1, b2);
+        }
+      } else {
+        for (int q = tid; q < Qs; q += MB) {
+          const bool u0 = used[2 * q], u1 = used[2 * q + 1];
+          if (u0 && u1) continue;
+          screen_pair<RA>(C, q, u0, u1, b1, r1, b2);
+        }
       }
       // best and second-best screen scores: warp shuffles, one barrier, then every
       // thread merges the per-warp results itself (double-buffered by step parity)
@@ -400,6 +437,15 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
   }
   // no CTA of a cluster exits while another may still read its shared memory
   if constexpr (CLU) cg::this_cluster().sync();
+  if constexpr (TM) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sh_tmem),
+                   "n"(kTmemCols)
+                   : "memory");
+  }
 }
 
 // Candidate pairs of one CTA slot: M candidates over CL CTAs, padded to 32 pairs (so the
@@ -423,13 +469,16 @@ struct MixVariant {
   int RA;
   bool SR;
   int CL;
+  bool TM = false;  // rows R .. R + RT - 1 also in tensor memory (RA == 0, CL == 1)
 };
 
 const void *mix_kernel(MixVariant v) {
   if (v.CL > 1)
     return v.RA ? reinterpret_cast<const void *>(select_mixed_kernel<RING_A, false, true>)
                 : reinterpret_cast<const void *>(select_mixed_kernel<0, false, true>);
-  if (!v.RA) return reinterpret_cast<const void *>(select_mixed_kernel<0, false, false>);
+  if (!v.RA)
+    return v.TM ? reinterpret_cast<const void *>(select_mixed_kernel<0, false, false, true>)
+                : reinterpret_cast<const void *>(select_mixed_kernel<0, false, false>);
   return v.SR ? reinterpret_cast<const void *>(select_mixed_kernel<RING_A, true, false>)
               : reinterpret_cast<const void *>(select_mixed_kernel<RING_A, false, false>);
 }
@@ -586,7 +635,24 @@ int mix_run(MixParams P, MixVariant v, const MixLayout &L, int G, char *w, int32
   P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(o);
   o += L.idx;
   P.CL = v.CL;
+  // tensor-memory rows in the instance without the ring (one CTA per location): 16, 8 or 4
+  // rows per pair for 1, 2, or 3-4 pairs per thread, so that each thread's rows fit its 64
+  // columns in whole loads of four rows; none where n leaves no rows past shared memory.
+  // LAGP_MIX_TMEM=0 turns it off (for measurements; no result changes).
+  P.RT = 0;
+  if (!v.RA && v.CL == 1 && mix_env("LAGP_MIX_TMEM") != 0) {
+    const int pp = (P.Qpad + MB - 1) / MB;
+    if (pp <= 4) {
+      v.TM = true;
+      P.RT = 4 * (4 / pp);
+    }
+  }
   P.R = mix_rows_in_smem(P.Qpad, P.nmax, v, di);
+  if (v.TM && P.nmax <= P.R) {
+    v.TM = false;
+    P.RT = 0;
+    P.R = mix_rows_in_smem(P.Qpad, P.nmax, v, di);
+  }
   P.fuse_pred = v.RA == 0 && v.CL == 1 &&
                 (size_t)P.R * P.Qpad * sizeof(float4) >= (size_t)P.nmax * (P.nmax + 2) * sizeof(double);
   const size_t smem = mix_smem_bytes(P.Qpad, P.nmax, P.R, v.RA, v.SR);
@@ -613,7 +679,10 @@ int mix_run(MixParams P, MixVariant v, const MixLayout &L, int G, char *w, int32
     e = cudaLaunchKernelExC(&cfg, mix_kernel(v), args);
     if (e != cudaSuccess) return cuda_status(e);
   } else if (!v.RA) {
-    select_mixed_kernel<0, false, false><<<G, MB, smem, stream>>>(P);
+    if (v.TM)
+      select_mixed_kernel<0, false, false, true><<<G, MB, smem, stream>>>(P);
+    else
+      select_mixed_kernel<0, false, false><<<G, MB, smem, stream>>>(P);
   } else if (v.SR) {
     select_mixed_kernel<RING_A, true, false><<<G, MB, smem, stream>>>(P);
   } else {
