@@ -318,6 +318,24 @@ int lagp_select_dev_noalloc(const double *X, const double *Z, int64_t N, int32_t
  * exponential.  x, y: n doubles (device).  No counterpart in the paper. */
 int lagp_exp_dev(const double *x, double *y, int64_t n, void *stream);
 
+/* Bounds checks of the checked build (the library built with -DLAGP_CHECKED,
+ * liblagp_checked.so): a stand-in for a memory sanitizer.  Its kernels compare every
+ * data-dependent index and every size taken from the launch (design indices against N,
+ * a location's n, candidate count and dimension against its scratch slot, the shared-memory
+ * layout against the launch's dynamic shared memory, tensor-memory columns against a
+ * thread's words) with its extent; a violation is recorded and the access skipped, and the
+ * location is abandoned.  Waits for the device, then returns in *count the violations since
+ * the last call and in *site, *index, *bound the first one (site codes: 1-5 kernel (a):
+ * survivor list, survivor design index, bucket scatter, bucket permutation, output index;
+ * 11, 13-15, 18, 20 the mixed ALC screen: candidate design index, n, candidate count,
+ * dimension, tensor-memory column, shared-memory layout; 21-25 the FP64 ALC kernel: n,
+ * candidate count, dimension, candidate design index, shared-memory layout; 31-32 the
+ * paper-form kernel: candidate design index, shared-memory layout), and clears the records.
+ * *checked = 1 in the checked build, 0 otherwise (where every count is 0).  Any output may
+ * be NULL. */
+int lagp_check_take(int32_t *checked, int64_t *count, int32_t *site, int64_t *index,
+                    int64_t *bound);
+
 /* Number of kernel launches this library has issued in this process (all entry
  * points, all threads).  Used to report how many of the library's kernels a timed
  * region launched. */

@@ -238,6 +238,33 @@ int lagp_select_dense_dev(const double *X, const double *Z, int64_t N, int32_t p
   return select_dense_launch(a, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
+int lagp_check_take(int32_t *checked, int64_t *count, int32_t *site, int64_t *index,
+                    int64_t *bound) {
+#ifdef LAGP_CHECKED
+  if (checked) *checked = 1;
+#else
+  if (checked) *checked = 0;
+#endif
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  int (*const takes[])(CheckRec *) = {knn_check_take, select_check_take, select_mixed_check_take,
+                                      select_dense_check_take};
+  CheckRec first = {0ull, 0, 0, 0};
+  unsigned long long total = 0ull;
+  for (auto take : takes) {
+    CheckRec r;
+    const int st = take(&r);
+    if (st) return st;
+    if (r.count && !first.count) first = r;
+    total += r.count;
+  }
+  if (count) *count = (int64_t)total;
+  if (site) *site = (int32_t)first.site;
+  if (index) *index = first.index;
+  if (bound) *bound = first.bound;
+  return LAGP_OK;
+}
+
 int lagp_select_rescore_count(const void *workspace, size_t workspace_bytes, int32_t method,
                               int32_t precision, int64_t *count, void *stream) {
   if (!count) return LAGP_ERR_INVALID_ARG;

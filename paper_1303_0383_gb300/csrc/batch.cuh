@@ -37,6 +37,7 @@ struct BatchView {
 // A location's parameters, resolved from the tables or the uniform values.
 struct LocParams {
   int64_t loc;
+  int64_t N;        // design rows (the extent design indices are checked against)
   const double *X, *Z, *x;
   int p, n, M, n0;
   double theta, theta_inv, onepg;
@@ -47,12 +48,14 @@ struct LocParams {
 __device__ __forceinline__ LocParams resolve_loc(const BatchView &B, int64_t q, const double *X,
                                                  const double *Z, const double *XX, int p, int n,
                                                  int M, int n0, double theta, double g,
-                                                 const int32_t *cand, int32_t *idx) {
+                                                 const int32_t *cand, int32_t *idx,
+                                                 int64_t N = INT64_MAX) {
   LocParams L;
   if (B.designs) {
     L.loc = B.order ? B.order[q] : q;
     const LocDesc d = B.locs[L.loc];
     const BatchDesign D = B.designs[d.design];
+    L.N = D.N;
     L.X = D.X; L.Z = D.Z; L.p = D.p; L.n = d.n; L.M = d.M; L.n0 = D.n0;
     L.theta = D.theta; L.theta_inv = 1.0 / D.theta; L.onepg = 1.0 + D.g;
     L.x = XX + L.loc * B.ldxx;
@@ -60,6 +63,7 @@ __device__ __forceinline__ LocParams resolve_loc(const BatchView &B, int64_t q, 
     L.idx = idx ? idx + d.idx_off : nullptr;
   } else {
     L.loc = q;
+    L.N = N;
     L.X = X; L.Z = Z; L.p = p; L.n = n; L.M = M; L.n0 = n0;
     L.theta = theta; L.theta_inv = 1.0 / theta; L.onepg = 1.0 + g;
     L.x = XX + q * p;

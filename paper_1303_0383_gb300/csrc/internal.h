@@ -166,6 +166,17 @@ int check_supported(int32_t method, int32_t precision);
 // Unique id of the calling thread's current CUDA context, 0 if none (api.cu).
 int current_context_id(unsigned long long *id);
 
+// Bounds-check records of the checked build (check.cuh): one per instrumented translation
+// unit, read and cleared by these (all zero in normal builds).
+struct CheckRec {
+  unsigned long long count;  // violations since the last take
+  long long site, index, bound;
+};
+int knn_check_take(CheckRec *out);
+int select_check_take(CheckRec *out);
+int select_mixed_check_take(CheckRec *out);
+int select_dense_check_take(CheckRec *out);
+
 // Map the last CUDA error to a library code.
 int cuda_status(cudaError_t e);
 

@@ -29,6 +29,7 @@
 #include <float.h>
 
 #include "batch.cuh"
+#include "check.cuh"
 #include "internal.h"
 
 namespace lagp {
@@ -357,7 +358,10 @@ __device__ bool bucket_order(const uint32_t *kh, const uint32_t *kl, const int32
   __syncthreads();
   if (*sh_flag) return false;
   // scatter: afterwards bound[b] is the end of bucket b (= the start of bucket b + 1)
-  for (int r = threadIdx.x; r < cnt; r += KB) perm[atomicAdd(&bound[bucket_of(r)], 1u)] = r;
+  for (int r = threadIdx.x; r < cnt; r += KB) {
+    const uint32_t at = atomicAdd(&bound[bucket_of(r)], 1u);
+    if (LAGP_CHK(at, cnt, 3)) perm[at] = r;
+  }
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += KB) {
     const uint32_t lo = b ? bound[b - 1] : 0u, hi = bound[b];
@@ -374,7 +378,10 @@ __device__ bool bucket_order(const uint32_t *kh, const uint32_t *kl, const int32
     }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < M; r += KB) out[r] = sidx[perm[r]];
+  for (int r = threadIdx.x; r < M; r += KB) {
+    const uint32_t pr = perm[r];
+    out[r] = LAGP_CHK(pr, cnt, 4) ? sidx[pr] : -1;
+  }
   return true;
 }
 
@@ -485,7 +492,8 @@ __global__ void __launch_bounds__(KB, 4) knn_kernel(const double *__restrict__ X
             uint32_t base = 0;
             if ((threadIdx.x & 31) == 0 && ball) base = atomicAdd(&sh_count, (uint32_t)__popc(ball));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (keep) sidx[base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u))] = (int32_t)kl[r];
+            const uint32_t at = base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u));
+            if (keep && LAGP_CHK(at, cap, 1)) sidx[at] = (int32_t)kl[r];
           }
           __syncthreads();
           cnt = (int)sh_count;
@@ -521,7 +529,7 @@ __global__ void __launch_bounds__(KB, 4) knn_kernel(const double *__restrict__ X
     if (cnt <= cap)
       for (int r = threadIdx.x; r < cnt; r += KB) {
         const int32_t i = sidx[r];
-        put_key(kh, kl, sidx, (uint32_t)r, sqdist_exact(xs, X + (size_t)i * p, p), i);
+        if (LAGP_CHK(i, N, 2)) put_key(kh, kl, sidx, (uint32_t)r, sqdist_exact(xs, X + (size_t)i * p, p), i);
       }
     __syncthreads();
     if (cnt > cap || cnt < M)  // too many ties at the boundary (or, defensively, too few)
@@ -539,7 +547,10 @@ __global__ void __launch_bounds__(KB, 4) knn_kernel(const double *__restrict__ X
       }
       __syncthreads();
       bitonic_sort(kh, kl, sidx, n2);
-      for (int r = threadIdx.x; r < M; r += KB) out[r] = sidx[r];
+      for (int r = threadIdx.x; r < M; r += KB) {
+        const int32_t v = sidx[r];
+        out[r] = LAGP_CHK(v, N, 5) ? v : -1;
+      }
     }
     __syncthreads();
   }
@@ -564,6 +575,8 @@ int knn_grid(int64_t T, int num_sms, size_t smem) {
 }
 
 }  // namespace
+
+int knn_check_take(CheckRec *out) { return check_take_here(out); }
 
 // Scratch layout: [bmax (256 B)] [Xf: p x N floats, dimension-major]
 size_t knn_workspace_bytes(int64_t N, int64_t T, int32_t ncand, int num_sms) {

@@ -11,6 +11,7 @@
 
 #include <math.h>
 
+#include "check.cuh"
 #include "ff.cuh"
 #include "ff2.cuh"
 #include "fp64_exp.cuh"
@@ -253,6 +254,10 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
   // with tensor memory: rows R .. jt-1 from there, jt .. j-1 from global memory
   const int jt = TM ? max(jr, min(C.j, C.R + C.RT)) : jr;
   const uint32_t ta = TM ? C.tb + (uint32_t)((q / nt) * C.RT * 4) : 0u;
+  // checked build: this pair's tensor-memory words end within the thread's 64 (the test is
+  // the same for a whole warp, whose pairs share q / nt)
+  if constexpr (TM)
+    if (!LAGP_CHK((q / nt + 1) * C.RT * 4 - 1, 64, 18)) return;
   // the first RA - 1 global rows start on their way (one copy group each); streamed rows
   // do not fit in L2 anyway, so they go evict-first and leave it to the data re-read every
   // step (candidate coordinates; 8-d workload 156.2 -> 140.5 ms)

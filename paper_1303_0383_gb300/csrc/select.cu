@@ -32,6 +32,7 @@
 #include <math.h>
 
 #include "batch.cuh"
+#include "check.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -42,6 +43,7 @@ constexpr int SB = 256;  // threads per CTA
 
 struct SelParams {
   const double *X, *Z;
+  int64_t N;       // design rows (uniform launches; batched ones take each design's)
   int p;
   const double *XX;
   int64_t T;
@@ -91,6 +93,10 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double *U = P.U + (size_t)blockIdx.x * nmax * Mpad;
   double *Xc = P.Xc + (size_t)blockIdx.x * P.pmax * Mpad;
+  // checked build: the layout above ends within the launch's dynamic shared memory
+  if (!LAGP_CHK(reinterpret_cast<unsigned char *>(sr + nmax) - reinterpret_cast<unsigned char *>(sm),
+                dynamic_smem_bytes() + 1u, 25))
+    return;
 
   for (;;) {
     __syncthreads();
@@ -98,9 +104,12 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
     __syncthreads();
     if (sh_loc >= P.T) break;
     const LocParams L = resolve_loc(P.B, sh_loc, P.X, P.Z, P.XX, P.p, P.n, P.M, P.n0, P.theta,
-                                    P.g, P.cand, P.idx);
+                                    P.g, P.cand, P.idx, P.N);
     const int64_t loc = L.loc;
     const int n = L.n, p = L.p, M = L.M;
+    // checked build: the location fits the slot (rows, candidates, coordinates)
+    if (!(LAGP_CHK(n - 1, nmax, 21) && LAGP_CHK(M - 1, Mpad, 22) && LAGP_CHK(p - 1, P.pmax, 23)))
+      continue;
     const int32_t *cnd = L.cand;
     if (tid < p) xl[tid] = L.x[tid];
     if (tid == 0) { sh_fail = 0; sh_vx = L.onepg; sh_psi = 0.0; sh_n = n; }
@@ -112,6 +121,12 @@ __global__ void __launch_bounds__(SB, 2) select_fp64_kernel(SelParams P) {
     // NN, and ALC without greedy steps (n0 == n), never look past rank n-1
     const int limit = ((P.method == LAGP_NN || n0e == n) && !P.start) ? n : M;
     for (int c = tid; c < limit; c += SB) {
+      if (!LAGP_CHK(cnd[c], L.N, 24)) {  // never read, never chosen
+        v[c] = 0.0;
+        covx[c] = 0.0;
+        used[c] = 1;
+        continue;
+      }
       const double *xc = L.X + (int64_t)cnd[c] * p;
       double acc = 0.0;
       for (int k = 0; k < p; k++) {
@@ -260,6 +275,8 @@ size_t sel_smem_bytes(int Mpad, int n) {
 
 }  // namespace
 
+int select_check_take(CheckRec *out) { return check_take_here(out); }
+
 size_t select_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int32_t method,
                               int32_t precision, int num_sms) {
   if (method == LAGP_MSPE)
@@ -291,7 +308,7 @@ int select_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStream_t s
   const int G = sel_grid(a.T, di.num_sms);
   char *w = static_cast<char *>(ws);
   SelParams P;
-  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
+  P.X = a.X; P.Z = a.Z; P.N = a.N; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.method = a.method;
   P.theta = a.theta;
   P.g = a.g;
@@ -337,7 +354,7 @@ int select_launch_on_grid(const SelectArgs &a, void *ws, size_t ws_bytes, int G,
   const int Mpad = mpad_of(a.M);
   char *w = static_cast<char *>(ws);
   SelParams P;
-  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
+  P.X = a.X; P.Z = a.Z; P.N = a.N; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.method = a.method;
   P.theta = a.theta;
   P.g = a.g;
@@ -402,7 +419,7 @@ int select_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, cudaStr
   const int Mpad = mpad_of(b.Mmax);
   char *w = static_cast<char *>(ws);
   SelParams P;
-  P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
+  P.X = nullptr; P.Z = nullptr; P.N = 0; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
   P.M = b.Mmax; P.Mpad = Mpad; P.n0 = 0; P.n = b.nmax; P.method = b.method;
   P.theta = 1.0; P.g = 0.0; P.nmax = b.nmax; P.pmax = b.pmax;
   P.B = BatchView{b.designs, b.locs, b.order, b.ldxx, nullptr, nullptr};

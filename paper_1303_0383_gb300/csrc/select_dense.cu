@@ -29,6 +29,7 @@
 // run past j without tests.
 #include <math.h>
 
+#include "check.cuh"
 #include "fp64_exp.cuh"
 #include "internal.h"
 
@@ -42,6 +43,7 @@ constexpr int kDenseMaxN = 128;
 
 struct DenseParams {
   const double *X, *Z;
+  int64_t N;
   int p;
   const double *XX;
   int64_t T;
@@ -82,6 +84,10 @@ __global__ void __launch_bounds__(DB, kDenseCtas) select_dense_kernel(DenseParam
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double *Kc = P.Kc + (size_t)blockIdx.x * n * Mpad;
   double *Xc = P.Xc + (size_t)blockIdx.x * p * Mpad;
+  // checked build: the layout above ends within the launch's dynamic shared memory
+  if (!LAGP_CHK(reinterpret_cast<unsigned char *>(used + Mpad) - reinterpret_cast<unsigned char *>(sm),
+                dynamic_smem_bytes() + 1u, 32))
+    return;
 
   for (;;) {
     __syncthreads();
@@ -103,6 +109,12 @@ __global__ void __launch_bounds__(DB, kDenseCtas) select_dense_kernel(DenseParam
     }
     // candidates' coordinates and K(x, c)
     for (int c = tid; c < M; c += DB) {
+      if (!LAGP_CHK(cnd[c], P.N, 31)) {  // never read, never chosen
+        kxc[c] = 0.0;
+        used[c] = 1;
+        for (int k = 0; k < p; k++) Xc[k * Mpad + c] = 0.0;
+        continue;
+      }
       const double *xc = P.X + (int64_t)cnd[c] * p;
       double acc = 0.0;
       for (int k = 0; k < p; k++) {
@@ -283,6 +295,8 @@ DenseLayout dense_layout(int64_t T, int p, int n, int M, int num_sms) {
 
 }  // namespace
 
+int select_dense_check_take(CheckRec *out) { return check_take_here(out); }
+
 int select_dense_max_n() { return kDenseMaxN; }
 
 size_t select_dense_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms) {
@@ -303,7 +317,7 @@ int select_dense_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   const int G = dense_grid(a.T, di.num_sms);
   char *w = static_cast<char *>(ws);
   DenseParams P;
-  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
+  P.X = a.X; P.Z = a.Z; P.N = a.N; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Mpad = Mpad; P.n0 = a.n0; P.n = a.n; P.ld = dense_ld(a.n);
   P.theta_inv = 1.0 / a.theta; P.onepg = 1.0 + a.g;
   P.queue = reinterpret_cast<int *>(w);

@@ -29,6 +29,7 @@
 #include <stdlib.h>
 
 #include "batch.cuh"
+#include "check.cuh"
 #include "mixed_screen.cuh"
 #include "predict_loc.cuh"
 
@@ -42,6 +43,7 @@ constexpr int kMaxCL = 8;          // CTAs per cluster in the cluster form
 
 struct MixParams {
   const double *X, *Z;
+  int64_t N;       // design rows (uniform launches; batched ones take each design's)
   int p;
   const double *XX;
   int64_t T;
@@ -114,6 +116,10 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
   float4 *Us = reinterpret_cast<float4 *>(used + P.Mpad);    // R x Qpad: first factor rows
   const int R = P.R;
   float4 *ring = Us + (size_t)R * Qpad + threadIdx.x;        // RA x MB: row ring
+  // checked build: the layout above ends within the launch's dynamic shared memory
+  if (!LAGP_CHK(reinterpret_cast<unsigned char *>(Us + (size_t)R * Qpad + (size_t)RA * MB) - smraw,
+                dynamic_smem_bytes() + 1u, 20))
+    return;
   __shared__ float tabh[64], tabl[64];
   __shared__ double etab[64];
   __shared__ double xl[kMaxP];
@@ -175,8 +181,11 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
     }
     if (qloc >= P.T) break;
     const LocParams L = resolve_loc(P.B, qloc, P.X, P.Z, P.XX, P.p, P.n, P.M, P.n0, P.theta,
-                                    P.g, P.cand, P.idx);
+                                    P.g, P.cand, P.idx, P.N);
     const int n = L.n, p = L.p, M = L.M;
+    // checked build: the location fits the slot (rows, candidates, coordinates)
+    if (!(LAGP_CHK(n - 1, nmax, 13) && LAGP_CHK(M - 1, CL * P.Mpad, 14) && LAGP_CHK(p - 1, P.pmax, 15)))
+      continue;
     const int32_t *cnd = L.cand;
     const ff onepg = ff_from_double(L.onepg);
     // the start design: the n0 nearest, or a saved design (augmentation)
@@ -200,7 +209,8 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
       for (int h = 0; h < 2; h++) {
         const int c = 2 * q + h;             // this CTA's index
         const int cgl = 2 * (q0 + q) + h;    // the location's candidate rank
-        const bool live = CLU ? (q < Ql && cgl < M) : (c < M);
+        bool live = CLU ? (q < Ql && cgl < M) : (c < M);
+        if (live && !LAGP_CHK(cnd[cgl], L.N, 11)) live = false;
         cv[h] = ff{0.0f, 0.0f};
         if (live) {
           const double *xc = L.X + (int64_t)cnd[cgl] * p;
@@ -701,6 +711,8 @@ int mix_run(MixParams P, MixVariant v, const MixLayout &L, int G, char *w, int32
 
 }  // namespace
 
+int select_mixed_check_take(CheckRec *out) { return check_take_here(out); }
+
 size_t select_mixed_workspace_bytes(int64_t T, int32_t p, int32_t n, int32_t ncand, int num_sms) {
   return mix_uniform_bytes(T, p, n, ncand, num_sms);
 }
@@ -723,7 +735,7 @@ int select_mixed_launch(const SelectArgs &a, void *ws, size_t ws_bytes, cudaStre
   const MixLayout L = mix_layout(G, a.p, a.n, Qpad, a.T, a.T * a.n, di.num_sms);
   if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
   MixParams P;
-  P.X = a.X; P.Z = a.Z; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
+  P.X = a.X; P.Z = a.Z; P.N = a.N; P.p = a.p; P.XX = a.XX; P.T = a.T; P.cand = a.cand;
   P.M = a.M; P.Qpad = Qpad; P.Mpad = 2 * Qpad; P.n0 = a.n0; P.n = a.n;
   P.theta = a.theta; P.theta_inv = 1.0 / a.theta; P.g = a.g; P.onepg = 1.0 + a.g;
   P.nmax = a.n; P.pmax = a.p;
@@ -751,7 +763,7 @@ int select_mixed_batch_launch(const BatchLaunch &b, void *ws, size_t ws_bytes, i
   const MixLayout L = mix_layout(G, b.pmax, b.nmax, Qpad, b.T, b.idx_total, di.num_sms);
   if (ws_bytes < L.total) return LAGP_ERR_INVALID_ARG;
   MixParams P;
-  P.X = nullptr; P.Z = nullptr; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
+  P.X = nullptr; P.Z = nullptr; P.N = 0; P.p = b.pmax; P.XX = b.XX; P.T = b.T; P.cand = b.cand;
   P.M = b.Mmax; P.Qpad = Qpad; P.Mpad = 2 * Qpad; P.n0 = 0; P.n = b.nmax;
   P.theta = 1.0; P.theta_inv = 1.0; P.g = 0.0; P.onepg = 1.0;
   P.nmax = b.nmax; P.pmax = b.pmax;

@@ -41,11 +41,12 @@ class LagpError(RuntimeError):
 
 
 def load(path: str | None = None):
-    """Load liblagp.so (building it first if it is missing or stale)."""
+    """Load liblagp.so (building it first if it is missing or stale); with the environment
+    variable LAGP_CHECKED=1, the checked build liblagp_checked.so instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _build.build()
+    path = path or _build.build(checked=os.environ.get("LAGP_CHECKED") == "1")
     if not os.path.exists(path):
         raise ImportError("liblagp.so not found at %s" % path)
     L = ctypes.CDLL(path)
@@ -65,6 +66,8 @@ def load(path: str | None = None):
     L.lagp_select_workspace_bytes.restype = sz
     L.lagp_select_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64, i32, i32,
                                   P, P, P, P, P, P, sz, P]
+    L.lagp_check_take.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.lagp_select_dense_workspace_bytes.argtypes = [i64, i32, i32, i32]
     L.lagp_select_dense_workspace_bytes.restype = sz
     L.lagp_select_dense_dev.argtypes = [P, P, i64, i32, P, i64, P, i32, i32, i32, f64, f64, P, P,
@@ -187,6 +190,17 @@ def lagp_select_dev(X, Z, XX, cand, n0, n, theta, g, method, precision, mean, s2
                                 _m(method), _pr(precision), _dp(mean), _dp(s2), _dp(var), _dp(idx),
                                 _dp(status), _dp(ws), ws.numel(), _stream(stream)),
          "lagp_select_dev")
+
+
+def lagp_check_take() -> dict:
+    """Bounds-check violations recorded since the last call (checked build; zeros otherwise):
+    {"checked": 0/1, "count", "site", "index", "bound"} -- waits for the device."""
+    c, n, st, i, b = (ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(),
+                      ctypes.c_int64())
+    _chk(load().lagp_check_take(ctypes.byref(c), ctypes.byref(n), ctypes.byref(st), ctypes.byref(i),
+                                ctypes.byref(b)), "lagp_check_take")
+    return {"checked": int(c.value), "count": int(n.value), "site": int(st.value),
+            "index": int(i.value), "bound": int(b.value)}
 
 
 def lagp_select_dense_workspace_bytes(T, p, n, ncand) -> int:

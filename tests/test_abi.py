@@ -185,3 +185,15 @@ def test_dense_form_arguments_on_the_host():
     # T = 0 does nothing and needs no buffers
     assert L.lagp_select_dense_dev(None, None, 100, 2, None, 0, None, 50, 6, 20, 0.5, 1e-6, None,
                                    None, None, None, None, None, 0, None) == 0
+
+
+def test_checked_build_compiles_and_identifies_itself():
+    # the bounds-checked build (nvcc cross-compiles it here) reports checked = 1, the normal
+    # build 0; both before any GPU work (the flag is set before the device is touched)
+    from paper_1303_0383_gb300 import build
+    for checked, want in ((True, 1), (False, 0)):
+        L = ctypes.CDLL(build.build(checked=checked))
+        flag = ctypes.c_int32(-1)
+        L.lagp_check_take.argtypes = [ctypes.c_void_p] * 5
+        L.lagp_check_take(ctypes.byref(flag), None, None, None, None)
+        assert flag.value == want
