@@ -246,18 +246,20 @@ struct StepCtx {
 // TM (instance without the ring): rows R .. R + RT - 1 are read from this thread's
 // tensor-memory words instead of L2 (they are still written to global memory, where the
 // step's pivot row is gathered from); the caller keeps every warp convergent.
+// ps: the pair's slot among this thread's pairs (q = threadIdx.x + ps * blockDim.x), given
+// by the caller's loop so that no division is needed here.
 template <int RA, bool TM = false>
 __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bool u1, float &b1,
-                                            int &r1, float &b2) {
+                                            int &r1, float &b2, int ps = 0) {
   const int nt = blockDim.x;
   const int jr = C.j < C.R ? C.j : C.R;  // rows R .. j-1 come from global memory
   // with tensor memory: rows R .. jt-1 from there, jt .. j-1 from global memory
   const int jt = TM ? max(jr, min(C.j, C.R + C.RT)) : jr;
-  const uint32_t ta = TM ? C.tb + (uint32_t)((q / nt) * C.RT * 4) : 0u;
+  const uint32_t ta = TM ? C.tb + (uint32_t)(ps * C.RT * 4) : 0u;
   // checked build: this pair's tensor-memory words end within the thread's 64 (the test is
-  // the same for a whole warp, whose pairs share q / nt)
+  // the same for a whole warp, whose pairs share ps)
   if constexpr (TM)
-    if (!LAGP_CHK((q / nt + 1) * C.RT * 4 - 1, 64, 18)) return;
+    if (!LAGP_CHK((ps + 1) * C.RT * 4 - 1, 64, 18)) return;
   // the first RA - 1 global rows start on their way (one copy group each); streamed rows
   // do not fit in L2 anyway, so they go evict-first and leave it to the data re-read every
   // step (candidate coordinates; 8-d workload 156.2 -> 140.5 ms)
@@ -313,12 +315,20 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
     for (int i = jr; i < jt; i += 4) {  // rows past jt are loaded but not used
       uint32_t tw[16];
       tmem_ld16(ta + (uint32_t)(4 * (i - C.R)), tw);
+      if (i + 4 <= jt) {  // a whole group (the usual case): no per-row tests
 #pragma unroll
-      for (int k = 0; k < 4; k++)
-        if (i + k < jt)
+        for (int k = 0; k < 4; k++)
           ff2acc_sub_prod(acc, C.srow4[i + k], C.srow2[i + k],
                           make_float4(__uint_as_float(tw[4 * k]), __uint_as_float(tw[4 * k + 1]),
                                       __uint_as_float(tw[4 * k + 2]), __uint_as_float(tw[4 * k + 3])));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+          if (i + k < jt)
+            ff2acc_sub_prod(acc, C.srow4[i + k], C.srow2[i + k],
+                            make_float4(__uint_as_float(tw[4 * k]), __uint_as_float(tw[4 * k + 1]),
+                                        __uint_as_float(tw[4 * k + 2]), __uint_as_float(tw[4 * k + 3])));
+      }
     }
   }
   if constexpr (RA == 0) {

@@ -317,10 +317,10 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
         // multiple of 32 (all within Qpad; those past Qs only update state nobody reads),
         // a pair skipped only when the whole warp's are used
         const int Q32 = (Qs + 31) & ~31;
-        for (int q = tid; q < Q32; q += MB) {
+        for (int q = tid, ps = 0; q < Q32; q += MB, ps++) {
           const bool u0 = used[2 * q], u1 = used[2 * q + 1];
           if (__all_sync(0xffffffffu, u0 && u1)) continue;
-          screen_pair<RA, true>(C, q, u0, u1, b1, r1, b2);
+          screen_pair<RA, true>(C, q, u0, u1, b1, r1, b2, ps);
         }
       } else {
         for (int q = tid; q < Qs; q += MB) {
