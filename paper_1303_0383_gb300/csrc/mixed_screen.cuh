@@ -243,9 +243,9 @@ struct StepCtx {
 // they stream through a ring of RA stages.  The ring pays where the rows come from DRAM
 // (large n x M); where they mostly hit L2 its bookkeeping costs more than it hides.
 // u0, u1: the pair's used flags (read once by the caller).
-// TM (instance without the ring): rows R .. R + RT - 1 are read from this thread's
-// tensor-memory words instead of L2 (they are still written to global memory, where the
-// step's pivot row is gathered from); the caller keeps every warp convergent.
+// TM: rows R .. R + RT - 1 are read from this thread's tensor-memory words instead of L2 or
+// the ring (they are still written to global memory, where the step's pivot row is
+// gathered from); the caller keeps every warp convergent.
 // ps: the pair's slot among this thread's pairs (q = threadIdx.x + ps * blockDim.x), given
 // by the caller's loop so that no division is needed here.
 template <int RA, bool TM = false>
@@ -268,8 +268,8 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
     polf = l2_evict_first_policy();
 #pragma unroll
     for (int st = 0; st < RA - 1; st++) {
-      if (jr + st < C.j)
-        cp_async16_l2_hint(C.ring + st * nt, C.U + (size_t)(jr + st) * C.Qpad + q, polf);
+      if (jt + st < C.j)
+        cp_async16_l2_hint(C.ring + st * nt, C.U + (size_t)(jt + st) * C.Qpad + q, polf);
       cp_async_commit();
     }
   }
@@ -347,7 +347,7 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
     for (; i < C.j; i++, ug += Q) ff2acc_sub_prod(acc, C.srow4[i], C.srow2[i], ld_l2_hint(ug, pol));
   } else {
     int sc = 0, sp = RA - 1;  // ring stages of rows i and i + RA - 1
-    for (int i = jr; i < C.j; i++) {
+    for (int i = jt; i < C.j; i++) {
       const int ip = i + RA - 1;
       if (ip < C.j) cp_async16_l2_hint(C.ring + sp * nt, C.U + (size_t)ip * C.Qpad + q, polf);
       cp_async_commit();
@@ -371,6 +371,9 @@ __device__ __forceinline__ void screen_pair(const StepCtx &C, int q, bool u0, bo
     }
   } else {
     ff2_store((C.j < C.R ? C.Us : C.U) + (size_t)C.j * C.Qpad + q, u);
+    if constexpr (TM)
+      if (C.j >= C.R && C.j < C.R + C.RT)
+        tmem_st4(ta + (uint32_t)(4 * (C.j - C.R)), make_float4(u.h.x, u.h.y, u.l.x, u.l.y));
   }
   const ff2 v0 = ff2_load(C.vp + q), c0 = ff2_load(C.cp + q);
   ff2 v = ff2_sub(v0, ff2_mul(u, u));

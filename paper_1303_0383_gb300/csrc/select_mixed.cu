@@ -88,8 +88,9 @@ __host__ __device__ constexpr int mix_minb(int RA, bool SR, bool CLU) {
 // TM: rows R .. R + RT - 1 of each candidate are also kept in the CTA's tensor memory (128
 // columns: RT = 16, 8 or 4 rows for 1, 2 or up to 4 pairs per thread) and the screen reads
 // them from there instead of L2 (GB300, 24 warps per SM, four 16-byte loads per thread:
-// about 200 cycles from tensor memory against about 580 for L2 hits).  Instance without the
-// ring and outside the cluster form only.
+// about 200 cycles from tensor memory against about 580 for L2 hits).  One CTA per location
+// only (not the cluster form); the ring instances run 4 CTAs per SM, which take all 512
+// columns, so the allocation never waits there either.
 // CLU: the cluster form.  The P.CL CTAs of a thread-block cluster share one location, CTA
 // `crank` holding the candidate pairs crank*Qc .. crank*Qc + Qc - 1 (its own v, cov, flags,
 // factor rows and coordinates); a step's pivot state -- v_j(s), cov_j(x,s), u_s and x_s -- is
@@ -99,7 +100,7 @@ __host__ __device__ constexpr int mix_minb(int RA, bool SR, bool CLU) {
 // CTA's rows fit in shared memory.  Every candidate's arithmetic is the same in both forms.
 template <int RA, bool SR, bool CLU, bool TM = false>
 __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel(MixParams P) {
-  static_assert(!TM || (RA == 0 && !CLU), "tensor-memory rows: instance without ring or cluster");
+  static_assert(!TM || !CLU, "tensor-memory rows: one CTA per location");
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Qpad = P.Qpad, nmax = P.nmax;
   constexpr int NW = SR ? 1 : MB / 32;                       // copies of the factor row
@@ -489,7 +490,10 @@ const void *mix_kernel(MixVariant v) {
   if (!v.RA)
     return v.TM ? reinterpret_cast<const void *>(select_mixed_kernel<0, false, false, true>)
                 : reinterpret_cast<const void *>(select_mixed_kernel<0, false, false>);
-  return v.SR ? reinterpret_cast<const void *>(select_mixed_kernel<RING_A, true, false>)
+  if (v.SR)
+    return v.TM ? reinterpret_cast<const void *>(select_mixed_kernel<RING_A, true, false, true>)
+                : reinterpret_cast<const void *>(select_mixed_kernel<RING_A, true, false>);
+  return v.TM ? reinterpret_cast<const void *>(select_mixed_kernel<RING_A, false, false, true>)
               : reinterpret_cast<const void *>(select_mixed_kernel<RING_A, false, false>);
 }
 
@@ -645,12 +649,12 @@ int mix_run(MixParams P, MixVariant v, const MixLayout &L, int G, char *w, int32
   P.idx = user_idx ? user_idx : reinterpret_cast<int32_t *>(o);
   o += L.idx;
   P.CL = v.CL;
-  // tensor-memory rows in the instance without the ring (one CTA per location): 16, 8 or 4
-  // rows per pair for 1, 2, or 3-4 pairs per thread, so that each thread's rows fit its 64
-  // columns in whole loads of four rows; none where n leaves no rows past shared memory.
+  // tensor-memory rows (one CTA per location): 16, 8 or 4 rows per pair for 1, 2, or 3-4
+  // pairs per thread, so that each thread's rows fit its 64 columns in whole loads of four
+  // rows; none where n leaves no rows past shared memory.
   // LAGP_MIX_TMEM=0 turns it off (for measurements; no result changes).
   P.RT = 0;
-  if (!v.RA && v.CL == 1 && mix_env("LAGP_MIX_TMEM") != 0) {
+  if (v.CL == 1 && mix_env("LAGP_MIX_TMEM") != 0) {
     const int pp = (P.Qpad + MB - 1) / MB;
     if (pp <= 4) {
       v.TM = true;
@@ -670,6 +674,20 @@ int mix_run(MixParams P, MixVariant v, const MixLayout &L, int G, char *w, int32
   cudaError_t e = cudaFuncSetAttribute(mix_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
+  if (v.TM) {
+    // every resident CTA holds kTmemCols of the SM's 512 tensor-memory columns: if more
+    // CTAs could be resident than that allows, an allocation would wait for a neighbour to
+    // finish, so such a launch keeps its rows in global memory instead
+    int k = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, mix_kernel(v), MB, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (k * kTmemCols > 512) {
+      v.TM = false;
+      P.RT = 0;
+      e = cudaFuncSetAttribute(mix_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
   e = cudaMemsetAsync(w, 0, 512, stream);  // work counter and re-score counter
   if (e != cudaSuccess) return cuda_status(e);
   if (v.CL > 1) {
@@ -694,9 +712,15 @@ int mix_run(MixParams P, MixVariant v, const MixLayout &L, int G, char *w, int32
     else
       select_mixed_kernel<0, false, false><<<G, MB, smem, stream>>>(P);
   } else if (v.SR) {
-    select_mixed_kernel<RING_A, true, false><<<G, MB, smem, stream>>>(P);
+    if (v.TM)
+      select_mixed_kernel<RING_A, true, false, true><<<G, MB, smem, stream>>>(P);
+    else
+      select_mixed_kernel<RING_A, true, false><<<G, MB, smem, stream>>>(P);
   } else {
-    select_mixed_kernel<RING_A, false, false><<<G, MB, smem, stream>>>(P);
+    if (v.TM)
+      select_mixed_kernel<RING_A, false, false, true><<<G, MB, smem, stream>>>(P);
+    else
+      select_mixed_kernel<RING_A, false, false><<<G, MB, smem, stream>>>(P);
   }
   g_launches.fetch_add(1);
   e = cudaGetLastError();

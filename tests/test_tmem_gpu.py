@@ -80,3 +80,16 @@ def test_tmem_rows_edge_cases():
         with tmem(True):
             got = gpu_predict(w, "alc", "mixed")
         _same(got, ref, w.name)
+
+
+# n x M past the row ring's threshold: the ring instances (per-warp row copies, or the shared
+# copy at large n), with 4 and 2 pairs per thread (4 and 8 rows in tensor memory)
+@pytest.mark.parametrize("M,n", [(2000, 60), (1000, 120), (2000, 160)])
+def test_tmem_rows_in_the_ring_instances_are_bitwise_the_global_rows(M, n):
+    w = inputs.random_case(700 + M + n, 30000, 3, 40, 6, n, M, d=0.08, g=1e-6)
+    with tmem(False):
+        ref = gpu_predict(w, "alc", "mixed")
+    with tmem(True):
+        got = gpu_predict(w, "alc", "mixed")
+    assert (got["status"] == 0).all()
+    _same(got, ref, (M, n))
