@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(DB, kDenseCtas) select_dense_kernel(DenseParam
       if (tid == 0) {
         double v = P.onepg;
         for (int k = 0; k < j; k++) v = fma(-ks[k], av[k], v);  // v_j(s)
-        if (!(v > 0.0)) {
+        // (a used pivot is a start-design candidate the checked build dropped)
+        if (!(v > 0.0) || used[s]) {
           sh_fail = 1;
         } else {
           sh_vinv = 1.0 / v;

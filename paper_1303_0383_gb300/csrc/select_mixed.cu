@@ -207,11 +207,15 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
     // cov_0(x,c) = K(x,c) in FP64
     for (int q = tid; q < Qpad; q += MB) {
       ff cv[2];
+      bool flagged[2] = {false, false};  // checked build: a design index past N
       for (int h = 0; h < 2; h++) {
         const int c = 2 * q + h;             // this CTA's index
         const int cgl = 2 * (q0 + q) + h;    // the location's candidate rank
         bool live = CLU ? (q < Ql && cgl < M) : (c < M);
-        if (live && !LAGP_CHK(cnd[cgl], L.N, 11)) live = false;
+        if (live && !LAGP_CHK(cnd[cgl], L.N, 11)) {
+          live = false;
+          flagged[h] = true;
+        }
         cv[h] = ff{0.0f, 0.0f};
         if (live) {
           const double *xc = L.X + (int64_t)cnd[cgl] * p;
@@ -235,7 +239,10 @@ __global__ void __launch_bounds__(MB, mix_minb(RA, SR, CLU)) select_mixed_kernel
         }
         used[c] = live ? 0 : 1;
       }
-      vp[q] = make_float4(onepg.h, onepg.h, onepg.l, onepg.l);
+      // (a flagged candidate gets v = 0, so that a start design holding it fails instead of
+      // reading its index)
+      vp[q] = make_float4(flagged[0] ? 0.0f : onepg.h, flagged[1] ? 0.0f : onepg.h,
+                          flagged[0] ? 0.0f : onepg.l, flagged[1] ? 0.0f : onepg.l);
       cp[q] = make_float4(cv[0].h, cv[1].h, cv[0].l, cv[1].l);
     }
     // Cluster form: the first steps read the start pivots' v, cov and coordinates from

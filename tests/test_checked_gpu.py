@@ -6,9 +6,9 @@ A child process runs the headline paths on small cases in the checked build -- k
 8192 candidates, both precisions (the tensor-memory and the row-ring instances of the mixed
 screen), the paper's form, uneven batches -- and must record no violation and choose the
 same designs as the normal build.  Then an out-of-range design index planted in a candidate
-list (past the start design, so every access it could reach is one the checks guard) must be
-reported with its site, index and extent, and the location served from its other
-candidates."""
+list must be reported with its site, index and extent: past the start design the location is
+served from its other candidates, inside it the location fails (every access the planted
+index could reach is one the checks guard)."""
 from __future__ import annotations
 
 import os
@@ -57,12 +57,14 @@ w = inputs.random_case(93, 3000, 2, 8, 4, 20, 200, d=0.3, g=1e-6)
 cand = knn(w, w.ncand)
 bad = w.N + 5
 cand[2, w.ncand - 1] = bad               # past the start design: never forced into it
+cand[5, 1] = bad                         # inside the start design (n0 = 4): that location fails
 out = []
 for method, prec, dense in (("alc", "mixed", False), ("alc", "fp64", False), ("alc", "fp64", True)):
     r = select(w, cand, method, prec, dense=dense)
     c = lagp.lagp_check_take()
     out.append((c["checked"], c["count"], c["site"], c["index"], c["bound"], int(r["status"][2]),
-                int((r["idx"][2] == bad).sum())))
+                int((r["idx"][2] == bad).sum()), int(r["status"][5]), int((r["idx"][5] == bad).sum()),
+                int((r["status"] == 0).sum())))
 print(out)
 '''
 
@@ -74,7 +76,10 @@ def test_checked_build_reports_a_planted_design_index():
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
     rows = eval(r.stdout.strip().splitlines()[-1])
     N = 3000
-    for (checked, count, site, index, bound, status, chosen), want in zip(rows, (11, 24, 31)):
-        assert checked == 1 and count >= 1, rows
+    for row, want in zip(rows, (11, 24, 31)):
+        checked, count, site, index, bound, status, chosen, status5, chosen5, served = row
+        assert checked == 1 and count >= 2, rows
         assert (site, index, bound) == (want, N + 5, N), rows
-        assert status == 0 and chosen == 0, rows
+        assert status == 0 and chosen == 0, rows                       # served without it
+        assert status5 == lagp.LAGP_ERR_NOT_PD and chosen5 == 0, rows  # failed, no index out
+        assert served == 7, rows                                       # the other locations
