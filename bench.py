@@ -906,6 +906,78 @@ def run_stagewise(args, world, rank):
     return print_stagewise(args, w, spec, variants, clocks, world)
 
 
+_BATCH_ORACLE: dict = {}
+
+
+def batched_accuracy(B, idx, mean, s2, var, n_sample=48):
+    """The parity protocol (oracle/parity.py) on a seeded sample of a batch's locations: each
+    against the oracle on its own design, n and candidate count.  The sample is drawn from
+    the locations with n <= 80 and at most 1500 candidates (the oracle's cost grows as
+    n^2 M: seconds per location at n = 200, M = 4000); the oracle's designs are computed once
+    per batch and shared by both precisions, on the host cores (ctypes calls release the
+    interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from oracle.parity import check_location
+    from paper_1303_0383_gb300.inputs import Workload
+    rng = np.random.default_rng(4)
+    elig = np.nonzero((B.n <= 80) & (B.ncand <= 1500))[0]
+    locs = np.sort(rng.choice(elig, size=min(n_sample, len(elig)), replace=False))
+    off = np.concatenate([[0], np.cumsum(B.n)]).astype(np.int64)
+
+    def one_workload(t):
+        W = B.designs[int(B.design_of[t])]
+        x = np.ascontiguousarray(B.XX[t, : W.p][None, :])
+        return Workload("batched location %d" % t, W.X, W.Z, x, n0=W.n0, n=int(B.n[t]),
+                        ncand=int(B.ncand[t]), d=W.d, g=W.g)
+
+    key = (B.name, B.T, tuple(locs))
+    if key not in _BATCH_ORACLE:
+        def solve(t):
+            w1 = one_workload(t)
+            cand = oracle.knn(w1.X, w1.XX, w1.ncand)[0]
+            return cand, oracle.local_design(w1.X, w1.Z, w1.XX[0], cand, w1.n0, w1.n, w1.d, w1.g, "alc")
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+            _BATCH_ORACLE[key] = list(ex.map(solve, locs))
+    from oracle.parity import CLAUSES
+    same = failed = forced = near = 0
+    errs = {"mean": [], "s2": [], "var": []}
+    by_clause: dict = {}
+    first = None
+    for t, (cand, ora) in zip(locs, _BATCH_ORACLE[key]):
+        try:
+            info = check_location(one_workload(t), 0, cand, idx[off[t]:off[t + 1]], mean[t], s2[t],
+                                  "alc", gpu_var=var[t], ora=ora)
+        except AssertionError as e:
+            failed += 1
+            first = first or str(e)[:300]
+            continue
+        same += not info["forced"]
+        forced += info["forced"]
+        near += info["near_ties"]
+        failed += not info["ok_vals"]
+        for k in errs:
+            errs[k].append(info["err_" + k])
+        for k2, c in enumerate(info["clauses"]):
+            if c:
+                e = info["adj_%d" % k2][0]
+                nv, mv = by_clause.get(c, (0, 0.0))
+                by_clause[c] = (nv + 1, max(mv, e))
+    out = {"locations": int(len(locs)), "selection_match_rate": same / max(len(locs), 1),
+           "forced_path_locations": forced, "near_tie_steps": near, "failed": failed,
+           "sample": "%d seeded locations with n <= 80 and at most 1500 candidates" % len(locs)}
+    for k, v in errs.items():
+        v = np.asarray(v) if v else np.zeros(1)
+        out["max_rel_err_" + k] = float(v.max())
+        out["median_rel_err_" + k] = float(np.median(v))
+    out["adjudicated"] = {CLAUSES[c]: {"values": nv, "max_rel_err": mv}
+                          for c, (nv, mv) in sorted(by_clause.items())}
+    if first:
+        out["first_failure"] = first
+    return out
+
+
 def measure_batched(args, prec, steps, warmup, batch_T):
     """Workload 4: uneven local problems over three resident designs in one persistent
     launch, CUDA-graph replay, launch shape tuned on the first batch."""
@@ -954,6 +1026,8 @@ def measure_batched(args, prec, steps, warmup, batch_T):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    acc = batched_accuracy(B, idx.cpu().numpy(), mean.cpu().numpy(), s2.cpu().numpy(),
+                           var.cpu().numpy())
     return {"metric": "local-GP predictions/sec, batched uneven problems", "value": T / (ms / 1e3),
             "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "dtype": "f32x2+f64" if prec == "mixed" else "f64",
@@ -962,7 +1036,8 @@ def measure_batched(args, prec, steps, warmup, batch_T):
                        "l2": "flushed between timed steps (256 MB write)"},
             "clocks": clocks,
             # the library's kernels per step (graph replays count the kernels they hold)
-            "gpu_launches": (lagp.lagp_launch_count() - launches0) / steps}
+            "gpu_launches": (lagp.lagp_launch_count() - launches0) / steps,
+            "accuracy_vs_oracle": acc}
 
 
 def run_batched(args):
