@@ -1049,6 +1049,56 @@ def run_batched(args):
     return 0
 
 
+_SERVE_ORACLE: dict = {}
+
+
+def served_accuracy(designs, ncand, picked):
+    """The parity protocol on served locations (the first location of every 23rd request at
+    the headline rate, at most 48): each against the oracle on its design, n and candidate
+    count.  picked: (design, x, n, result row) tuples.  The oracle's designs are cached by
+    request, so both precisions (which serve the same seeded requests) share them."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from oracle.parity import check_location
+    from paper_1303_0383_gb300.inputs import Workload
+
+    def workload(d, x, n):
+        W = designs[d]
+        return Workload("served location", W.X, W.Z, np.ascontiguousarray(x[None, :]), n0=W.n0,
+                        n=n, ncand=ncand[d], d=W.d, g=W.g)
+
+    keys = [(d, x.tobytes(), n) for d, x, n, _ in picked]
+    todo = [(k, d, x, n) for k, (d, x, n, _) in zip(keys, picked) if k not in _SERVE_ORACLE]
+
+    def solve(item):
+        _, d, x, n = item
+        w1 = workload(d, x, n)
+        cand = oracle.knn(w1.X, w1.XX, w1.ncand)[0]
+        return cand, oracle.local_design(w1.X, w1.Z, w1.XX[0], cand, w1.n0, w1.n, w1.d, w1.g, "alc")
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for item, res in zip(todo, ex.map(solve, todo)):
+            _SERVE_ORACLE[item[0]] = res
+    same = failed = 0
+    worst = {"mean": 0.0, "s2": 0.0, "var": 0.0}
+    for k, (d, x, n, r) in zip(keys, picked):
+        cand, ora = _SERVE_ORACLE[k]
+        try:
+            info = check_location(workload(d, x, n), 0, cand, r["idx"], r["mean"], r["s2"], "alc",
+                                  gpu_var=r["var"], ora=ora)
+        except AssertionError:
+            failed += 1
+            continue
+        same += not info["forced"]
+        failed += not info["ok_vals"]
+        for q in worst:
+            worst[q] = max(worst[q], info["err_" + q])
+    return {"locations": len(picked), "selection_match_rate": same / max(len(picked), 1),
+            "failed": failed, "max_rel_err_mean": worst["mean"], "max_rel_err_s2": worst["s2"],
+            "max_rel_err_var": worst["var"],
+            "sample": "the first location of every 23rd request at the headline rate"}
+
+
 def measure_serving(rates, seconds, precs):
     """Workload 5: Poisson arrivals of requests (1..4096 locations, log-uniform) against
     the three resident designs with n in {50, 100}; p50/p99 latency and throughput per
@@ -1077,9 +1127,10 @@ def measure_serving(rates, seconds, precs):
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
         per_rate = {}
+        picked = []
         for lam in rates:
             rng = np.random.default_rng(int(lam))
-            sent = []
+            sent, reqs = [], []
             start = time.perf_counter()
             t_next = 0.0
             while t_next < seconds:
@@ -1091,14 +1142,18 @@ def measure_serving(rates, seconds, precs):
                 if t_next > now:
                     time.sleep(t_next - now)
                 sent.append((srv.submit(d, x, n, ncand[d]), L))
+                reqs.append((d, x, n))
                 t_next += rng.exponential(L / lam)   # arrivals carry L locations at rate lam
             lat, locs = [], 0
-            for rid, L in sent:
+            for k, (rid, L) in enumerate(sent):
                 srv.wait(rid, -1)
                 r = srv.results(rid)
                 assert (r["status"] == 0).all()
                 lat.append(r["latency_ms"])
                 locs += L
+                if lam == max(rates) and k % 23 == 0 and len(picked) < 48:
+                    d, x, n = reqs[k]
+                    picked.append((d, x[0].copy(), n, {q: r[q][0] for q in ("idx", "mean", "s2", "var")}))
             wall = time.perf_counter() - start
             lat = np.array(lat)
             per_rate[str(int(lam))] = {
@@ -1110,7 +1165,8 @@ def measure_serving(rates, seconds, precs):
         st = srv.stats()
         srv.close()
         results[prec] = {"rates": per_rate, "slots": st["slots"], "max_inflight": st["max_inflight"],
-                         "batches": st["batches"], "clocks": clocks}
+                         "batches": st["batches"], "clocks": clocks,
+                         "accuracy_vs_oracle": served_accuracy(B.designs, ncand, picked)}
     top = str(int(max(rates)))
     head = "mixed" if "mixed" in results else precs[0]
     return {"metric": "serving p99 ms (Poisson arrivals, 1..4096 locations per request)",
