@@ -215,7 +215,8 @@ __device__ __forceinline__ void tmem_st4(uint32_t ta, float4 v) {
                : "memory");
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
-constexpr int kTmemCols = 128;  // columns per CTA (at most 3 CTAs per SM hold 384 of 512)
+constexpr int kTmemCols = 128;  // columns per CTA: 3 or 4 resident CTAs per SM hold 384 or 512,
+                                // and the host checks the residency before it launches
 
 // One step of the screen for one candidate pair of this thread (Sec. 3.2 update, in
 // float-float): K(s, c) from the squared distance, the new factor entry
