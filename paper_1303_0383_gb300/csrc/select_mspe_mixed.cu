@@ -93,7 +93,24 @@ __device__ __forceinline__ void split_rows(const double *A1, const double *x1, c
       double s1 = 0.0, s2 = 0.0;
       const int h = hi(i);
       const unsigned long long pol = l2_evict_last_policy();
-      for (int m = lo(i) + c; m < h; m += SPLIT) {
+      int m = lo(i) + c;
+      // eight terms' loads are issued before their multiply-adds, which keep the order of
+      // the one-term loop (the same sums, bit for bit): one L2 round trip per eight terms
+      // instead of one per term
+      for (; m + 7 * SPLIT < h; m += 8 * SPLIT) {
+        double v1[8], v2[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          v1[u] = ld_l2_hint(a1 + m + u * SPLIT, pol);
+          v2[u] = a2 ? ld_l2_hint(a2 + m + u * SPLIT, pol) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          s1 = fma(v1[u], x1[m + u * SPLIT], s1);
+          if (a2) s2 = fma(v2[u], x2[m + u * SPLIT], s2);
+        }
+      }
+      for (; m < h; m += SPLIT) {
         s1 = fma(ld_l2_hint(a1 + m, pol), x1[m], s1);
         if (a2) s2 = fma(ld_l2_hint(a2 + m, pol), x2[m], s2);
       }
